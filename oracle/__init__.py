@@ -1,0 +1,180 @@
+"""FP64 CPU oracle of the 3D RSF level-set iteration (arXiv 2404.02813).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline / reference legs of ``bench.py`` may import this package.
+The product path (``paper_2404_02813_gb300``) never imports it, and the two
+share no code: the C source ``rsf_oracle.c`` restates every equation on its
+own.
+
+Functions follow the paper's equations (see the header of ``rsf_oracle.c``
+for the full list and for the readings taken where the paper is silent):
+
+* :func:`taps`        Eq. (7): normalised discrete Gaussian, R = round(2 sigma)
+* :func:`conv3`       Eq. (6) convolution K*F, separable x -> y -> z, zero padding
+* :func:`heaviside`   Eq. (10)
+* :func:`dirac`       Eq. (14)
+* :func:`stencils`    Eqs. (3)-(4): curvature div(grad phi/|grad phi|), Laplacian
+* :func:`step`        one iteration, Eqs. (1), (6), (11)-(14)
+* :func:`evolve`      ``iters`` iterations
+* :func:`point_next`  one voxel of :func:`step` by direct triple sums
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rsf_oracle.c")
+_LIBS = {False: os.path.join(_HERE, "liboracle.so"), True: os.path.join(_HERE, "liboracle_omp.so")}
+
+DUMP_NAMES = ("H", "f1", "f2", "e1", "e2", "g", "kappa", "lap")
+
+
+def build(force: bool = False) -> None:
+    """Compile the single-thread and the OpenMP builds of the oracle with gcc.
+
+    Both use -O2 without fast-math, so IEEE double arithmetic is kept.
+    """
+    for omp, out in _LIBS.items():
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            continue
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+               _SRC, "-o", out + ".tmp", "-lm"]
+        if omp:
+            cmd.insert(1, "-fopenmp")
+        subprocess.run(cmd, check=True)
+        os.replace(out + ".tmp", out)
+
+
+_loaded = {}
+
+
+def _lib(omp: bool = False):
+    if omp in _loaded:
+        return _loaded[omp]
+    build()
+    lib = ctypes.CDLL(_LIBS[omp])
+    dp = ctypes.POINTER(ctypes.c_double)
+    i64 = ctypes.c_int64
+    d = ctypes.c_double
+    lib.rsf_oracle_radius.argtypes = [d]
+    lib.rsf_oracle_radius.restype = ctypes.c_int
+    lib.rsf_oracle_taps.argtypes = [d, dp]
+    lib.rsf_oracle_taps.restype = ctypes.c_int
+    lib.rsf_oracle_conv3.argtypes = [dp, dp, i64, i64, i64, d]
+    lib.rsf_oracle_conv3.restype = None
+    lib.rsf_oracle_heaviside.argtypes = [d, d]
+    lib.rsf_oracle_heaviside.restype = d
+    lib.rsf_oracle_dirac.argtypes = [d, d]
+    lib.rsf_oracle_dirac.restype = d
+    lib.rsf_oracle_stencils.argtypes = [dp, i64, i64, i64, dp, dp]
+    lib.rsf_oracle_stencils.restype = None
+    lib.rsf_oracle_step.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, dp]
+    lib.rsf_oracle_step.restype = None
+    lib.rsf_oracle_evolve.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, ctypes.c_int]
+    lib.rsf_oracle_evolve.restype = None
+    lib.rsf_oracle_point_next.argtypes = [dp, dp, i64, i64, i64, i64, i64, i64, d, d, d, d, d, d, d]
+    lib.rsf_oracle_point_next.restype = d
+    lib.rsf_oracle_dump_slots.argtypes = []
+    lib.rsf_oracle_dump_slots.restype = ctypes.c_int
+    _loaded[omp] = lib
+    return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _vol(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim != 3:
+        raise ValueError("expected a 3-D [nz, ny, nx] array")
+    return a
+
+
+def radius(sigma: float) -> int:
+    return int(_lib().rsf_oracle_radius(float(sigma)))
+
+
+def taps(sigma: float) -> np.ndarray:
+    R = radius(sigma)
+    g = np.zeros(2 * R + 1, dtype=np.float64)
+    _lib().rsf_oracle_taps(float(sigma), _dp(g))
+    return g
+
+
+def conv3(F, sigma: float, omp: bool = False) -> np.ndarray:
+    F = _vol(F)
+    nz, ny, nx = F.shape
+    out = np.empty_like(F)
+    _lib(omp).rsf_oracle_conv3(_dp(F), _dp(out), nx, ny, nz, float(sigma))
+    return out
+
+
+def heaviside(u, eps: float = 1.0) -> np.ndarray:
+    f = _lib().rsf_oracle_heaviside
+    u = np.asarray(u, dtype=np.float64)
+    return np.vectorize(lambda v: f(float(v), float(eps)), otypes=[np.float64])(u)
+
+
+def dirac(u, eps: float = 1.0) -> np.ndarray:
+    f = _lib().rsf_oracle_dirac
+    u = np.asarray(u, dtype=np.float64)
+    return np.vectorize(lambda v: f(float(v), float(eps)), otypes=[np.float64])(u)
+
+
+def stencils(phi, omp: bool = False):
+    """Return (kappa, laplacian) of ``phi``."""
+    phi = _vol(phi)
+    nz, ny, nx = phi.shape
+    kap = np.empty_like(phi)
+    lap = np.empty_like(phi)
+    _lib(omp).rsf_oracle_stencils(_dp(phi), nx, ny, nz, _dp(kap), _dp(lap))
+    return kap, lap
+
+
+def _params(p: dict):
+    return (float(p["sigma"]), float(p["eps"]), float(p["lambda1"]), float(p["lambda2"]),
+            float(p["nu"]), float(p["mu"]), float(p["dt"]))
+
+
+def step(I, phi, params: dict, dump: bool = False, omp: bool = False):
+    """One iteration. Returns phi_next, or (phi_next, {stage: array}) with ``dump``."""
+    I = _vol(I)
+    phi = _vol(phi)
+    if I.shape != phi.shape:
+        raise ValueError("I and phi shapes differ")
+    nz, ny, nx = I.shape
+    out = np.empty_like(phi)
+    lib = _lib(omp)
+    nslots = lib.rsf_oracle_dump_slots()
+    buf: Optional[np.ndarray] = np.empty((nslots,) + I.shape, dtype=np.float64) if dump else None
+    lib.rsf_oracle_step(_dp(I), _dp(phi), _dp(out), nx, ny, nz, *_params(params),
+                        _dp(buf) if dump else None)
+    if dump:
+        return out, {name: buf[i] for i, name in enumerate(DUMP_NAMES)}
+    return out
+
+
+def evolve(I, phi0, params: dict, iters: int, omp: bool = False) -> np.ndarray:
+    I = _vol(I)
+    phi0 = _vol(phi0)
+    if I.shape != phi0.shape:
+        raise ValueError("I and phi0 shapes differ")
+    nz, ny, nx = I.shape
+    out = np.empty_like(phi0)
+    _lib(omp).rsf_oracle_evolve(_dp(I), _dp(phi0), _dp(out), nx, ny, nz, *_params(params), int(iters))
+    return out
+
+
+def point_next(I, phi, params: dict, x: int, y: int, z: int) -> float:
+    """phi_{n+1} at voxel (x, y, z) by direct triple sums (no separable passes)."""
+    I = _vol(I)
+    phi = _vol(phi)
+    nz, ny, nx = I.shape
+    return float(_lib().rsf_oracle_point_next(_dp(I), _dp(phi), nx, ny, nz, int(x), int(y), int(z),
+                                              *_params(params)))

@@ -1,0 +1,251 @@
+"""Seeded synthetic vessel-network volumes and initial level sets.
+
+These stand in for the paper's micro-CT, light-sheet and knife-edge / milling
+microscopy data (Sec. 5.2), which are not available.  The module holds input
+generation only -- no step of the level-set method -- and is the one module
+shared by the product tests, the benchmark and the oracle tests.
+
+Recipe (every volume): a branching random walk lays down capsule segments
+(segment length U[6, 20] voxels, direction jitter <= 40 degrees per segment,
+branch probability 0.3, radius uniform in the workload's range); each capsule
+is rasterised with partial-volume occupancy clip(r - d + 0.5, 0, 1), where d
+is the distance of the voxel centre from the segment, and capsules are
+max-composited (so the order does not matter); the occupancy is blurred by a
+separable Gaussian point-spread function, mapped to intensity
+background + (foreground - background) * occupancy, given noise, clipped and
+rounded to the storage type.  Random streams are numpy PCG64 seeded with
+1000 * workload + brick.
+
+Arrays are numpy [nz, ny, nx] (x fastest), the layout of the C-ABI.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Optional, Tuple
+
+import numpy as np
+
+try:  # the point-spread blur and the box mean; scipy is present on both machines
+    from scipy import ndimage as _ndi
+except Exception:  # pragma: no cover
+    _ndi = None
+
+
+def rng_for(workload: int, brick: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(1000 * int(workload) + int(brick)))
+
+
+# --------------------------------------------------------------- segments
+
+def _unit(v: np.ndarray) -> np.ndarray:
+    return v / np.linalg.norm(v)
+
+
+def _random_dir(rng: np.random.Generator) -> np.ndarray:
+    return _unit(rng.normal(size=3))
+
+
+def _jitter(rng: np.random.Generator, d: np.ndarray, max_deg: float, min_deg: float = 0.0) -> np.ndarray:
+    """Rotate unit vector d by an angle in [min_deg, max_deg] about a random perpendicular axis."""
+    a = np.deg2rad(rng.uniform(min_deg, max_deg))
+    p = rng.normal(size=3)
+    p -= p.dot(d) * d
+    p = _unit(p)
+    return _unit(np.cos(a) * d + np.sin(a) * p)
+
+
+@dataclass
+class Segments:
+    """Capsules: endpoints p0, p1 (n, 3) in (x, y, z) voxel units and radii r (n,)."""
+    p0: np.ndarray
+    p1: np.ndarray
+    r: np.ndarray
+
+    def __len__(self) -> int:
+        return int(self.r.shape[0])
+
+
+def vessel_segments(rng: np.random.Generator, extent_xyz: Tuple[float, float, float], n_segments: int,
+                    r_range: Tuple[float, float], seg_len=(6.0, 20.0), jitter_deg: float = 40.0,
+                    p_branch: float = 0.3) -> Segments:
+    """Branching random walk inside the box [0, extent) (x, y, z)."""
+    ext = np.asarray(extent_xyz, dtype=np.float64)
+    p0s, p1s, rs = [], [], []
+    stack = []
+    while len(rs) < n_segments:
+        if not stack:
+            stack.append((rng.uniform(0.0, 1.0, size=3) * ext, _random_dir(rng),
+                          rng.uniform(r_range[0], r_range[1])))
+        p, d, r = stack.pop()
+        q = p + rng.uniform(seg_len[0], seg_len[1]) * d
+        p0s.append(p)
+        p1s.append(q)
+        rs.append(r)
+        if np.all(q >= -2.0) and np.all(q <= ext + 2.0):
+            if rng.random() < p_branch:
+                rb = float(np.clip(r * rng.uniform(0.6, 1.0), r_range[0], r_range[1]))
+                stack.insert(0, (q, _jitter(rng, d, 90.0, 30.0), rb))
+            stack.append((q, _jitter(rng, d, jitter_deg), r))
+    return Segments(np.array(p0s), np.array(p1s), np.array(rs))
+
+
+def rasterize(seg: Segments, origin_xyz, shape_zyx) -> np.ndarray:
+    """Partial-volume occupancy of the box [origin, origin + shape) (float32, [z, y, x])."""
+    oz, oy, ox = (int(origin_xyz[2]), int(origin_xyz[1]), int(origin_xyz[0]))
+    nz, ny, nx = (int(s) for s in shape_zyx)
+    occ = np.zeros((nz, ny, nx), dtype=np.float32)
+    lo = np.minimum(seg.p0, seg.p1) - seg.r[:, None] - 1.0
+    hi = np.maximum(seg.p0, seg.p1) + seg.r[:, None] + 1.0
+    org = np.array([ox, oy, oz], dtype=np.float64)
+    top = org + np.array([nx, ny, nz], dtype=np.float64)
+    hit = np.all(hi >= org, axis=1) & np.all(lo <= top - 1, axis=1)
+    for i in np.nonzero(hit)[0]:
+        a = np.maximum(np.floor(lo[i]).astype(np.int64), org.astype(np.int64))
+        b = np.minimum(np.ceil(hi[i]).astype(np.int64) + 1, top.astype(np.int64))
+        if np.any(b <= a):
+            continue
+        xs = np.arange(a[0], b[0], dtype=np.float64)
+        ys = np.arange(a[1], b[1], dtype=np.float64)
+        zs = np.arange(a[2], b[2], dtype=np.float64)
+        Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+        p, q, r = seg.p0[i], seg.p1[i], seg.r[i]
+        v = q - p
+        vv = max(float(v.dot(v)), 1e-12)
+        t = np.clip(((X - p[0]) * v[0] + (Y - p[1]) * v[1] + (Z - p[2]) * v[2]) / vv, 0.0, 1.0)
+        dx = X - (p[0] + t * v[0])
+        dy = Y - (p[1] + t * v[1])
+        dz = Z - (p[2] + t * v[2])
+        o = np.clip(r - np.sqrt(dx * dx + dy * dy + dz * dz) + 0.5, 0.0, 1.0).astype(np.float32)
+        sl = (slice(a[2] - oz, b[2] - oz), slice(a[1] - oy, b[1] - oy), slice(a[0] - ox, b[0] - ox))
+        np.maximum(occ[sl], o, out=occ[sl])
+    return occ
+
+
+def _blur(occ: np.ndarray, sig_zyx) -> np.ndarray:
+    if _ndi is None:
+        raise RuntimeError("scipy.ndimage is required for the point-spread blur")
+    return _ndi.gaussian_filter(occ, sigma=sig_zyx, mode="reflect", truncate=3.0).astype(np.float32)
+
+
+# ------------------------------------------------------------ workloads
+
+@dataclass
+class RSFParams:
+    sigma: float = 3.0
+    eps: float = 1.0
+    lambda1: float = 1.0
+    lambda2: float = 2.0
+    nu: float = 0.004 * 255.0 ** 2
+    mu: float = 1.0
+    dt: float = 0.1
+    iters: int = 50
+    c0: float = 2.0
+
+    def as_dict(self) -> dict:
+        return dict(sigma=self.sigma, eps=self.eps, lambda1=self.lambda1, lambda2=self.lambda2,
+                    nu=self.nu, mu=self.mu, dt=self.dt)
+
+
+def box_phi0(shape_zyx, box: int, c0: float = 2.0) -> np.ndarray:
+    """+c0 inside a centred box of edge `box`, -c0 elsewhere (float32)."""
+    phi = np.full(shape_zyx, -c0, dtype=np.float32)
+    sl = tuple(slice((n - box) // 2, (n - box) // 2 + box) for n in shape_zyx)
+    phi[sl] = c0
+    return phi
+
+
+def mean_rule_phi0(vol: np.ndarray, c0: float = 2.0) -> np.ndarray:
+    """+c0 where the 3x3x3 box mean of the image (clamped borders) exceeds the image mean."""
+    if _ndi is None:
+        raise RuntimeError("scipy.ndimage is required for the box mean")
+    v = vol.astype(np.float64)
+    m = _ndi.uniform_filter(v, size=3, mode="nearest")
+    return np.where(m > v.mean(), c0, -c0).astype(np.float32)
+
+
+def tree_volume_u8(shape_zyx=(64, 64, 64), workload: int = 1, brick: int = 0, n_segments: int = 40,
+                   r_range=(1.0, 4.0), fg: float = 200.0, bg: float = 30.0, psf: float = 1.0,
+                   noise: float = 15.0) -> np.ndarray:
+    """Small uint8 vessel tree (the 64^3 parity workload)."""
+    rng = rng_for(workload, brick)
+    nz, ny, nx = shape_zyx
+    seg = vessel_segments(rng, (nx, ny, nz), n_segments, r_range)
+    occ = _blur(rasterize(seg, (0, 0, 0), shape_zyx), (psf, psf, psf))
+    img = bg + (fg - bg) * occ + rng.normal(0.0, noise, size=occ.shape)
+    return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+
+
+def lightsheet_volume_u16(shape_zyx=(512, 512, 512), workload: int = 2, brick: int = 0,
+                          n_segments: Optional[int] = None, r_range=(0.5, 3.0), peak: float = 4000.0,
+                          background: float = 300.0, psf_xy: float = 1.0, psf_z: float = 2.5) -> np.ndarray:
+    """uint16 light-sheet-like volume: anisotropic PSF and Poisson shot noise.
+
+    ~2000 segments per 512^3; smaller shapes scale the count with the volume.
+    """
+    rng = rng_for(workload, brick)
+    nz, ny, nx = shape_zyx
+    if n_segments is None:
+        n_segments = max(8, int(round(2000 * (nz * ny * nx) / 512 ** 3)))
+    seg = vessel_segments(rng, (nx, ny, nz), n_segments, r_range)
+    occ = _blur(rasterize(seg, (0, 0, 0), shape_zyx), (psf_z, psf_xy, psf_xy))
+    lam = background + peak * occ
+    img = rng.poisson(lam)
+    return np.clip(img, 0, 65535).astype(np.uint16)
+
+
+# ----------------------------------------------------- batched bricks
+
+@dataclass
+class BrickSpec:
+    origin_xyz: Tuple[int, int, int]
+    core_xyz: Tuple[int, int, int]
+    halo: int
+
+    @property
+    def padded_zyx(self) -> Tuple[int, int, int]:
+        cx, cy, cz = self.core_xyz
+        h = 2 * self.halo
+        return (cz + h, cy + h, cx + h)
+
+
+@dataclass
+class MicroCTField:
+    """A virtual uint16 micro-CT-like volume rasterised only where bricks are requested."""
+    extent_xyz: Tuple[int, int, int] = (2048, 2048, 1024)
+    workload: int = 3
+    r_range: Tuple[float, float] = (1.0, 6.0)
+    fg: float = 1200.0
+    bg: float = 400.0
+    noise: float = 80.0
+    psf: float = 1.0
+    density: float = 2000.0 / 512 ** 3   # segments per voxel, as the light-sheet volume
+    seg: Segments = field(init=False)
+
+    def __post_init__(self):
+        rng = rng_for(self.workload, 0)
+        ex, ey, ez = self.extent_xyz
+        n = int(self.density * ex * ey * ez)
+        self.seg = vessel_segments(rng, (ex, ey, ez), n, self.r_range)
+
+    def brick(self, spec: BrickSpec, brick_index: int) -> np.ndarray:
+        """The padded brick (halo voxels included) as uint16 [z, y, x]."""
+        m = int(np.ceil(3 * self.psf)) + 1
+        nz, ny, nx = spec.padded_zyx
+        ox, oy, oz = (o - spec.halo - m for o in spec.origin_xyz)
+        occ = rasterize(self.seg, (ox, oy, oz), (nz + 2 * m, ny + 2 * m, nx + 2 * m))
+        occ = _blur(occ, (self.psf,) * 3)[m:m + nz, m:m + ny, m:m + nx]
+        rng = rng_for(self.workload, 1 + brick_index)
+        img = self.bg + (self.fg - self.bg) * occ + rng.normal(0.0, self.noise, size=occ.shape)
+        return np.clip(np.rint(img), 0, 65535).astype(np.uint16)
+
+
+def brick_specs(n_bricks: int = 256, core_range=(64, 192), halo: int = 12,
+                extent_xyz=(2048, 2048, 1024), workload: int = 3) -> list:
+    """Uneven, non-cubic brick cores drawn U[core_range] per axis at random positions."""
+    rng = rng_for(workload, 100000)
+    out = []
+    for _ in range(n_bricks):
+        core = tuple(int(c) for c in rng.integers(core_range[0], core_range[1] + 1, size=3))
+        org = tuple(int(rng.integers(halo, e - c - halo)) for e, c in zip(extent_xyz, core))
+        out.append(BrickSpec(org, core, halo))
+    return out
