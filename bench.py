@@ -1,0 +1,319 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 RSF level-set path.
+
+A step is one rsf_evolve call: set-up (centring, K*1 profiles) plus `iters`
+RSF iterations over one synthetic volume, inputs resident in HBM.  The
+default workload is the 512^3 uint16 light-sheet-like vessel volume at
+sigma = 3 with 200 iterations; the metric is GVoxel-iterations/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl rsf|reference]
+
+Under torchrun (N > 1) every rank evolves its own volume (weak scaling, no
+collective on the data path); rank 0 prints one JSON line with the whole-job
+throughput (voxel-iterations of all ranks / max time over ranks).
+`--impl reference` times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic HBM bytes per voxel and launch of each per-iteration kernel: the
+# fields it must read once and write once (FP32), independent of tiling.
+ALGO_BYTES_PER_VOXEL = {
+    "rsf_a_x": 4 + 4 + 16,   # phi, I -> four H-product fields
+    "rsf_a_y": 16 + 16,
+    "rsf_a_z": 16 + 8,       # four fields -> a, b
+    "rsf_b_x": 8 + 8,
+    "rsf_b_y": 8 + 8,
+    "rsf_b_z": 8 + 4 + 4 + 4,  # a, b, I, phi -> phi'
+}
+
+# DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
+# per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
+# it was captured from; reported only while that file is unchanged.
+NCU_TRAFFIC = {}
+
+P_LIGHTSHEET = 4300.0
+
+
+def _kernel_source_sha() -> str:
+    p = os.path.join(ROOT, "paper_2404_02813_gb300", "csrc", "rsf_passes.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([s.strip() for s in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) >= 9:
+                for n, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name: str, rank: int):
+    from paper_2404_02813_gb300 import synth
+    if name == "lightsheet512":
+        vol = synth.lightsheet_volume_u16((512, 512, 512), brick=rank)
+        params = dict(sigma=3.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P_LIGHTSHEET ** 2, mu=1.0, dt=0.1)
+        iters = 200
+    elif name == "lightsheet512_s5":
+        vol = synth.lightsheet_volume_u16((512, 512, 512), brick=rank)
+        params = dict(sigma=5.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P_LIGHTSHEET ** 2, mu=1.0, dt=0.1)
+        iters = 200
+    elif name == "tree64":
+        vol = synth.tree_volume_u8(brick=rank)
+        params = synth.RSFParams().as_dict()
+        iters = 50
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    phi0 = synth.box_phi0(vol.shape, 32) if name == "tree64" else synth.mean_rule_phi0(vol)
+    return vol, phi0, params, iters
+
+
+def workload_desc(name, vol, params, iters):
+    nz, ny, nx = vol.shape
+    return {"workload": f"{name}: plain RSF, {nx}x{ny}x{nz} {vol.dtype.name} synthetic vessel volume, "
+                        f"sigma={params['sigma']:g} ({2 * int(np.floor(2 * params['sigma'] + 0.5)) + 1} taps), "
+                        f"{iters} iterations per step",
+            "voxels": int(vol.size), "iters_per_step": iters, "sigma": params["sigma"],
+            "l2": "inputs larger than L2 (each FP32 field 4*voxels bytes)"}
+
+
+def cpu_baseline(vol, phi0, params, budget_s=15.0):
+    """The FP64 oracle (single thread) on a bounded corner crop of the same volume."""
+    import oracle
+    c = 64
+    I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
+    ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
+    t0 = time.perf_counter()
+    oracle.evolve(I, ph, params, 1)
+    t1 = time.perf_counter() - t0
+    its = max(1, min(40, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.evolve(I, ph, params, its)
+    dt = time.perf_counter() - t0
+    return {"value": I.size * its / dt / 1e9, "unit": "GVoxel-iterations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{c}^3 corner crop of the workload volume, {its} iterations, FP64 single-thread C (-O2)"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle on host cores; rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+    vol, phi0, params, iters = make_workload(args.workload, 0)
+    c = 48
+    I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
+    ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
+    its = 4
+    for _ in range(args.warmup):
+        oracle.evolve(I, ph, params, 1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.evolve(I, ph, params, its)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    v = I.size * its * args.steps / T / 1e9
+    sample = f"{c}^3 corner crop, {its} iterations per step, FP64 single-thread C oracle"
+    out = {"impl": "reference", "metric": "GVoxel-iterations/s", "value": v, "unit": "GVoxel-iterations/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_desc(args.workload, vol, params, iters),
+           "cpu_baseline": {"value": v, "unit": "GVoxel-iterations/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "GVoxel-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="rsf", choices=["rsf", "reference"])
+    ap.add_argument("--workload", default="lightsheet512", choices=["lightsheet512", "lightsheet512_s5", "tree64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "rsf":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2404_02813_gb300 import rsf
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    vol, phi0, params, iters = make_workload(args.workload, rank)
+    n_vox = vol.size
+    v = torch.from_numpy(vol).cuda()
+    ph0 = torch.from_numpy(phi0).cuda()
+    out = torch.empty_like(ph0)
+    ctx = rsf.Context(local)
+    stream = torch.cuda.ExternalStream(ctx.stream_handle)
+
+    for _ in range(args.warmup):
+        ctx.evolve(v, ph0, params, iters, out=out)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.prof_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.evolve(v, ph0, params, iters, out=out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.prof_get()
+    ctx.prof_enable(False)
+
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    total_vox_it = n_vox * iters * args.steps * world
+    value = total_vox_it / (ms_max / 1e3) / 1e9
+
+    # end to end through the same call with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        vh = torch.from_numpy(vol).pin_memory()
+        ph = torch.from_numpy(phi0).pin_memory()
+        oh = torch.empty_like(ph).pin_memory()
+        ctx.evolve(vh, ph, params, iters, out=oh)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.evolve(vh, ph, params, iters, out=oh)
+        torch.cuda.synchronize()
+        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": total_vox_it / float(te.item()) / 1e9, "unit": "GVoxel-iterations/s",
+               "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + ph.numel() * 4),
+               "d2h_bytes_per_step": int(oh.numel() * 4)}
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        dom = max(prof, key=lambda k: prof[k][1])
+        n_l, tot_ms = prof[dom]
+        avg_s = tot_ms / max(n_l, 1) / 1e3
+        algo = ALGO_BYTES_PER_VOXEL[dom] * n_vox
+        achieved = algo / avg_s / 1e9
+        sha = _kernel_source_sha()
+        tr = NCU_TRAFFIC.get(dom)
+        traffic = tr["bytes_per_voxel"] * n_vox if tr and tr.get("source_sha") == sha else None
+        launches_per_step = 3 + len(ALGO_BYTES_PER_VOXEL) * iters
+        line = {
+            "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded vessel-network volume, light-sheet-like)",
+            "config": dict(workload_desc(args.workload, vol, params, iters),
+                           parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                         "traffic": traffic, "algo_bytes_per_launch": algo,
+                         "avg_launch_ms": avg_s * 1e3, "launches": n_l},
+            "kernels": {k: {"launches": n, "ms": round(m, 3), "share": round(m / max(sum(x[1] for x in prof.values()), 1e-9), 4)}
+                        for k, (n, m) in prof.items() if n},
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(vol, phi0, params)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

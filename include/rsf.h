@@ -1,0 +1,140 @@
+/*
+ * rsf.h -- C ABI of the GB300 (sm_103a) 3D region-scalable-fitting (RSF)
+ * level-set library `librsf.so`.
+ *
+ * The library evolves a level-set function phi over a voxel volume I with the
+ * explicit update of arXiv 2404.02813, Eq. (1):
+ *
+ *     phi_{n+1} = phi_n + dt * ( mu * (L phi - kappa) + delta_eps(phi) * (nu * kappa - g) )
+ *
+ * with (Sec. 3) the Heaviside H_eps of Eq. (10) and its derivative delta_eps of
+ * Eq. (14); the local fits f_1 = K*(H I) / K*H and f_2 = K*((1-H) I) / K*(1-H)
+ * of Eq. (6), K the normalised discrete Gaussian of Eq. (7) with radius
+ * R = round(2 sigma) and zero padding outside the volume; the data terms
+ * e_i = (K*1) I^2 - 2 I (K*f_i) + K*(f_i^2) and g = lambda1 e_1 - lambda2 e_2
+ * (the directional forces of Eqs. (11)-(12)); kappa = div(grad phi / (|grad phi| + 1e-10))
+ * and the 7-point Laplacian L (Eqs. (3)-(4), (13)) with central differences and
+ * reflect-101 boundaries (-1 -> 1, n -> n-2).  Every term is evaluated at phi_n.
+ *
+ * Conventions shared by every entry point
+ *  - Volumes are dense, x fastest: element (x, y, z) is at (z*ny + y)*nx + x.
+ *  - Each dimension must be >= 4; nx*ny*nz must be <= 2^34.
+ *  - Pointers may be host or device memory of the context's device; the
+ *    library tells them apart with the CUDA runtime.  Host pointers are
+ *    staged through device buffers the library owns.
+ *  - The caller owns every pointer it passes.  The library owns every device
+ *    buffer it allocates (working fields, staging copies); they are charged
+ *    against the context's HBM budget and freed by rsf_destroy.
+ *  - No entry point throws, aborts or exits.  Errors are returned as a
+ *    negative rsf_status; rsf_last_error() then describes the last one on the
+ *    calling thread.
+ *  - Arithmetic is FP32 on the GPU with FP32 accumulation in every
+ *    convolution; no step runs in FP64 on the GPU.
+ */
+#ifndef RSF_H
+#define RSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rsf_ctx rsf_ctx; /* opaque; one per device */
+
+typedef int32_t rsf_status;
+#define RSF_OK 0
+#define RSF_PENDING 1
+#define RSF_E_INVAL (-1)     /* bad argument: null pointer, dim < 4, NaN or non-positive sigma/eps/dt, iters < 0 */
+#define RSF_E_NOMEM (-2)     /* the HBM budget or a device allocation was exceeded */
+#define RSF_E_CUDA (-3)      /* a CUDA runtime call failed; see rsf_last_error() */
+#define RSF_E_TIMEOUT (-4)   /* a bounded wait expired */
+#define RSF_E_NOTFOUND (-5)  /* unknown ticket */
+#define RSF_E_BUSY (-6)      /* queue full */
+#define RSF_E_CANCELLED (-7) /* request cancelled */
+
+typedef enum { RSF_U8 = 0, RSF_U16 = 1, RSF_F32 = 2 } rsf_dtype;
+
+/* Storage precision of I and the convolved fields (phi is always FP32). */
+typedef enum { RSF_STORE_F32 = 0, RSF_STORE_BF16 = 1, RSF_STORE_F16 = 2 } rsf_storage;
+
+/*
+ * rsf_create -- open a context on CUDA device `device`.
+ *   out               receives the context (set to NULL on failure).
+ *   hbm_budget_bytes  upper bound on the device memory the context may hold
+ *                     at once; 0 means 90% of the device's free memory.
+ *   flags             reserved, must be 0.
+ * The context owns one CUDA stream (see rsf_stream) on which all its work runs.
+ * Errors: RSF_E_INVAL (out NULL, flags != 0), RSF_E_CUDA (no such device).
+ */
+rsf_status rsf_create(rsf_ctx **out, int device, uint64_t hbm_budget_bytes, uint32_t flags);
+
+/* rsf_destroy -- wait for the context's work, free every buffer it owns, and
+ * release it.  NULL is ignored. */
+void rsf_destroy(rsf_ctx *ctx);
+
+/* rsf_stream -- the context's cudaStream_t (as void*), for callers that time
+ * or order work around the library's launches. */
+void *rsf_stream(rsf_ctx *ctx);
+
+/*
+ * rsf_evolve -- run `iters` iterations of Eq. (1) from phi0 and write the
+ * result to phi_out.  Blocking: returns once phi_out holds the result.
+ *   volume   nx*ny*nz image values of type vt (RSF_U8, RSF_U16 or RSF_F32).
+ *   phi0     nx*ny*nz FP32 initial level set (phi > 0 is the H side, fit f_1).
+ *   phi_out  nx*ny*nz FP32 result; may alias phi0.
+ *   sigma    Gaussian width (> 0); R = round(2 sigma) must be <= 16.
+ *   eps      Heaviside width (> 0).
+ *   lambda1, lambda2  weights of e_1 and e_2.
+ *   nu       weight of the curvature term delta * kappa.
+ *   mu       weight of the regulariser L phi - kappa.
+ *   dt       time step (> 0).
+ *   iters    number of iterations (>= 0; 0 copies phi0 to phi_out).
+ * Set-up work (centring of I, K*I, the K*1 profiles) runs once per call.
+ * Errors: RSF_E_INVAL, RSF_E_NOMEM, RSF_E_CUDA.
+ */
+rsf_status rsf_evolve(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                      const float *phi0, float *phi_out, float sigma, float eps, float lambda1, float lambda2,
+                      float nu, float mu, float dt, int32_t iters);
+
+/*
+ * rsf_step_stages -- one iteration from phi with the intermediate fields
+ * written out, for checking each stage against a reference.
+ *   stages   host or device buffer of RSF_NSTAGES * nx*ny*nz floats,
+ *            slot s at offset s*nx*ny*nz, in the order of rsf_stage_id.
+ *   phi_next nx*ny*nz FP32 result of the iteration.
+ * Other arguments as rsf_evolve.  Errors as rsf_evolve.
+ */
+typedef enum {
+    RSF_STAGE_F1 = 0,   /* local fit f_1 (Eq. 6, H side) */
+    RSF_STAGE_F2 = 1,   /* local fit f_2 (Eq. 6, 1-H side) */
+    RSF_STAGE_G = 2,    /* g = lambda1 e_1 - lambda2 e_2 */
+    RSF_STAGE_KAPPA = 3,/* curvature div(grad phi / |grad phi|) */
+    RSF_STAGE_LAP = 4,  /* 7-point Laplacian of phi */
+    RSF_NSTAGES = 5
+} rsf_stage_id;
+
+rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                           const float *phi, float *phi_next, float *stages, float sigma, float eps,
+                           float lambda1, float lambda2, float nu, float mu, float dt);
+
+/*
+ * Kernel timing.  While enabled, the context records a CUDA event pair on its
+ * stream around every launch of its per-iteration kernels; rsf_prof_get
+ * returns, for the kernel named `kernel` (see rsf_prof_name), the number of
+ * launches and their summed device time in milliseconds since the last
+ * rsf_prof_enable(ctx, 1).  Errors: RSF_E_INVAL (unknown kernel index).
+ */
+rsf_status rsf_prof_enable(rsf_ctx *ctx, int32_t on);
+int32_t rsf_prof_count(void);
+const char *rsf_prof_name(int32_t kernel);
+rsf_status rsf_prof_get(rsf_ctx *ctx, int32_t kernel, int64_t *launches, double *total_ms);
+
+/* Thread-local description of the last error returned on this thread. */
+const char *rsf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSF_H */

@@ -1,0 +1,387 @@
+// rsf_api.cu -- the extern "C" boundary of librsf.so (declared in include/rsf.h):
+// contexts, the HBM-budgeted workspace, host/device pointer handling, the
+// blocking evolve call of Eq. (1) iterated, stage dumps and kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "rsf.h"
+#include "rsf_internal.h"
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_last_error;
+
+static rsf_status fail(rsf_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static rsf_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(RSF_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define RSF_CUDA(call)                                             \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+extern "C" const char *rsf_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------- profiler
+
+namespace rsf {
+
+const char *kernel_name(int id) {
+    static const char *names[KID_COUNT] = {"rsf_a_x", "rsf_a_y", "rsf_a_z", "rsf_b_x", "rsf_b_y", "rsf_b_z"};
+    return (id >= 0 && id < KID_COUNT) ? names[id] : nullptr;
+}
+
+cudaEvent_t Profiler::take() {
+    if (used == pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        pool.push_back(e);
+    }
+    return pool[used++];
+}
+
+void Profiler::begin(int id) {
+    open_id = id;
+    open_a = take();
+    if (open_a) cudaEventRecord(open_a, stream);
+}
+
+void Profiler::end() {
+    cudaEvent_t b = take();
+    if (open_a && b) {
+        cudaEventRecord(b, stream);
+        recs.push_back({open_id, open_a, b});
+    }
+    open_a = nullptr;
+}
+
+void Profiler::reset() {
+    recs.clear();
+    used = 0;
+}
+
+void Profiler::release() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+    recs.clear();
+    used = 0;
+}
+
+}  // namespace rsf
+
+// ----------------------------------------------------------------- context
+
+struct rsf_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+
+    rsf::Fields f;
+    long long cap_n = 0;     // elements per big field currently allocated
+    long long cap_prof = 0;  // profile floats allocated
+    void *staging = nullptr; // device copy of a host volume
+    size_t staging_cap = 0;
+    float *dump = nullptr;   // device stage dump for host destinations
+    size_t dump_cap = 0;
+    rsf::Profiler prof;
+};
+
+static rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
+    if (c->used + bytes > c->budget)
+        return fail(RSF_E_NOMEM, "allocation of %zu bytes exceeds the HBM budget (%llu of %llu bytes in use)", bytes,
+                    (unsigned long long)c->used, (unsigned long long)c->budget);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(RSF_E_NOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->used += bytes;
+    return RSF_OK;
+}
+
+static void dev_free(rsf_ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    c->used -= std::min<uint64_t>(c->used, bytes);
+}
+
+static constexpr int kBigFields = 11;  // I, phi[2], t[8]
+
+static void free_fields(rsf_ctx *c) {
+    size_t fb = sizeof(float) * (size_t)c->cap_n;
+    dev_free(c, c->f.I, fb);
+    for (float *&p : c->f.phi) { dev_free(c, p, fb); p = nullptr; }
+    for (float *&p : c->f.t) { dev_free(c, p, fb); p = nullptr; }
+    c->f.I = nullptr;
+    c->cap_n = 0;
+    dev_free(c, c->f.prof, sizeof(float) * (size_t)c->cap_prof);
+    c->f.prof = nullptr;
+    c->cap_prof = 0;
+}
+
+static rsf_status ensure_fields(rsf_ctx *c, int nx, int ny, int nz) {
+    rsf::Dims d{nx, ny, nz, (long long)nx * ny, (long long)nx * ny * nz};
+    if (d.n > c->cap_n) {
+        free_fields(c);
+        size_t fb = sizeof(float) * (size_t)d.n;
+        if ((uint64_t)kBigFields * fb + c->used > c->budget)
+            return fail(RSF_E_NOMEM, "volume of %lld voxels needs %llu bytes of working fields; budget %llu, in use %llu",
+                        d.n, (unsigned long long)kBigFields * fb, (unsigned long long)c->budget,
+                        (unsigned long long)c->used);
+        rsf_status st;
+        if ((st = dev_alloc(c, (void **)&c->f.I, fb))) return st;
+        for (float *&p : c->f.phi)
+            if ((st = dev_alloc(c, (void **)&p, fb))) return st;
+        for (float *&p : c->f.t)
+            if ((st = dev_alloc(c, (void **)&p, fb))) return st;
+        c->cap_n = d.n;
+    }
+    long long np = (long long)nx + ny + nz;
+    if (np > c->cap_prof) {
+        dev_free(c, c->f.prof, sizeof(float) * (size_t)c->cap_prof);
+        c->f.prof = nullptr;
+        rsf_status st = dev_alloc(c, (void **)&c->f.prof, sizeof(float) * np);
+        if (st) return st;
+        c->cap_prof = np;
+    }
+    if (!c->f.cs) {
+        rsf_status st = dev_alloc(c, (void **)&c->f.cs, sizeof(float) * 4);
+        if (st) return st;
+        st = dev_alloc(c, (void **)&c->f.partials, sizeof(float) * 3 * rsf::kStatBlocks);
+        if (st) return st;
+    }
+    c->f.d = d;
+    return RSF_OK;
+}
+
+// True when p is memory the device can use in place (device or managed).
+static bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static size_t dtype_size(rsf_dtype vt) { return vt == RSF_U8 ? 1 : (vt == RSF_U16 ? 2 : 4); }
+
+// Device-resident copy of the volume (the caller's own pointer when it already is one).
+static rsf_status device_volume(rsf_ctx *c, const void *volume, rsf_dtype vt, long long n, const void **out) {
+    if (on_device(volume)) {
+        *out = volume;
+        return RSF_OK;
+    }
+    size_t bytes = dtype_size(vt) * (size_t)n;
+    if (bytes > c->staging_cap) {
+        dev_free(c, c->staging, c->staging_cap);
+        c->staging = nullptr;
+        c->staging_cap = 0;
+        rsf_status st = dev_alloc(c, &c->staging, bytes);
+        if (st) return st;
+        c->staging_cap = bytes;
+    }
+    RSF_CUDA(cudaMemcpyAsync(c->staging, volume, bytes, cudaMemcpyDefault, c->stream));
+    *out = c->staging;
+    return RSF_OK;
+}
+
+static rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz, const void *phi0,
+                             const void *phi_out, float sigma, float eps, float dt, int32_t iters) {
+    if (!volume || !phi0 || !phi_out) return fail(RSF_E_INVAL, "null volume, phi0 or phi_out pointer");
+    if (vt != RSF_U8 && vt != RSF_U16 && vt != RSF_F32) return fail(RSF_E_INVAL, "unknown volume dtype %d", (int)vt);
+    const int64_t lim = 1 << 20;
+    if (nx < 4 || ny < 4 || nz < 4 || nx > lim || ny > lim || nz > lim)
+        return fail(RSF_E_INVAL, "each dimension must lie in [4, 2^20]; got %lld x %lld x %lld", (long long)nx,
+                    (long long)ny, (long long)nz);
+    if ((double)nx * (double)ny * (double)nz > 17179869184.0)
+        return fail(RSF_E_INVAL, "nx*ny*nz exceeds 2^34");
+    if ((double)ny * (double)nz >= 2147483648.0) return fail(RSF_E_INVAL, "ny*nz must be below 2^31");
+    if (!(sigma > 0.f) || !std::isfinite(sigma)) return fail(RSF_E_INVAL, "sigma must be positive and finite");
+    if ((int)std::floor(2.0 * sigma + 0.5) > rsf::RMAX)
+        return fail(RSF_E_INVAL, "kernel radius round(2 sigma) = %d exceeds %d", (int)std::floor(2.0 * sigma + 0.5),
+                    rsf::RMAX);
+    if (!(eps > 0.f) || !std::isfinite(eps)) return fail(RSF_E_INVAL, "eps must be positive and finite");
+    if (!(dt > 0.f) || !std::isfinite(dt)) return fail(RSF_E_INVAL, "dt must be positive and finite");
+    if (iters < 0) return fail(RSF_E_INVAL, "iters must be >= 0");
+    return RSF_OK;
+}
+
+// Normalised taps of Eq. (7): exp(-k^2/(2 sigma^2)) / sum, R = round(2 sigma).
+static rsf::Taps make_taps(float sigma) {
+    rsf::Taps t{};
+    t.R = (int)std::floor(2.0 * (double)sigma + 0.5);
+    double w[2 * rsf::RMAX + 1], s = 0.0;
+    for (int k = -t.R; k <= t.R; ++k) {
+        w[k + t.R] = std::exp(-(double)k * k / (2.0 * (double)sigma * (double)sigma));
+        s += w[k + t.R];
+    }
+    for (int k = 0; k < 2 * t.R + 1; ++k) t.g[k] = (float)(w[k] / s);
+    return t;
+}
+
+extern "C" rsf_status rsf_create(rsf_ctx **out, int device, uint64_t hbm_budget_bytes, uint32_t flags) {
+    if (!out) return fail(RSF_E_INVAL, "out is null");
+    *out = nullptr;
+    if (flags != 0) return fail(RSF_E_INVAL, "flags must be 0");
+    int n = 0;
+    RSF_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(RSF_E_CUDA, "no CUDA device %d (%d present)", device, n);
+    RSF_CUDA(cudaSetDevice(device));
+    size_t fr = 0, tot = 0;
+    RSF_CUDA(cudaMemGetInfo(&fr, &tot));
+    rsf_ctx *c = new rsf_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    c->prof.stream = c->stream;
+    *out = c;
+    return RSF_OK;
+}
+
+extern "C" void rsf_destroy(rsf_ctx *c) {
+    if (!c) return;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cudaSetDevice(c->device);
+        cudaStreamSynchronize(c->stream);
+        free_fields(c);
+        dev_free(c, c->f.cs, sizeof(float) * 4);
+        dev_free(c, c->f.partials, sizeof(float) * 3 * rsf::kStatBlocks);
+        dev_free(c, c->staging, c->staging_cap);
+        dev_free(c, c->dump, c->dump_cap);
+        c->prof.release();
+        cudaStreamDestroy(c->stream);
+    }
+    delete c;
+}
+
+extern "C" void *rsf_stream(rsf_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+// Shared body of rsf_evolve and rsf_step_stages.
+static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                      const float *phi0, float *phi_out, float *stages, float sigma, float eps, float lambda1,
+                      float lambda2, float nu, float mu, float dt, int32_t iters) {
+    RSF_CUDA(cudaSetDevice(c->device));
+    rsf_status st = ensure_fields(c, (int)nx, (int)ny, (int)nz);
+    if (st) return st;
+    rsf::Fields &f = c->f;
+    const long long n = f.d.n;
+    float *dump = nullptr;
+    if (stages) {
+        if (on_device(stages)) {
+            dump = stages;
+        } else {
+            size_t bytes = sizeof(float) * (size_t)n * RSF_NSTAGES;
+            if (bytes > c->dump_cap) {
+                dev_free(c, c->dump, c->dump_cap);
+                c->dump = nullptr;
+                c->dump_cap = 0;
+                if ((st = dev_alloc(c, (void **)&c->dump, bytes))) return st;
+                c->dump_cap = bytes;
+            }
+            dump = c->dump;
+        }
+    }
+    const void *vol = nullptr;
+    if ((st = device_volume(c, volume, vt, n, &vol))) return st;
+    const rsf::Taps taps = make_taps(sigma);
+    const rsf::Coeffs co{eps, lambda1, lambda2, nu, mu, dt};
+    RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream));
+    RSF_CUDA(cudaMemcpyAsync(f.phi[0], phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    int cur = 0;
+    for (int it = 0; it < iters; ++it) {
+        cudaError_t e = rsf::iterate_passes(taps, co, f, f.phi[cur], f.phi[cur ^ 1], it == iters - 1 ? dump : nullptr,
+                                            &c->prof, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+        cur ^= 1;
+    }
+    RSF_CUDA(cudaMemcpyAsync(phi_out, f.phi[cur], sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    if (stages && dump != stages)
+        RSF_CUDA(cudaMemcpyAsync(stages, dump, sizeof(float) * n * RSF_NSTAGES, cudaMemcpyDefault, c->stream));
+    RSF_CUDA(cudaStreamSynchronize(c->stream));
+    return RSF_OK;
+}
+
+extern "C" rsf_status rsf_evolve(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                                 const float *phi0, float *phi_out, float sigma, float eps, float lambda1,
+                                 float lambda2, float nu, float mu, float dt, int32_t iters) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    rsf_status st = check_args(volume, vt, nx, ny, nz, phi0, phi_out, sigma, eps, dt, iters);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return run(c, volume, vt, nx, ny, nz, phi0, phi_out, nullptr, sigma, eps, lambda1, lambda2, nu, mu, dt, iters);
+}
+
+extern "C" rsf_status rsf_step_stages(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny,
+                                      int64_t nz, const float *phi, float *phi_next, float *stages, float sigma,
+                                      float eps, float lambda1, float lambda2, float nu, float mu, float dt) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    if (!stages) return fail(RSF_E_INVAL, "null stages pointer");
+    rsf_status st = check_args(volume, vt, nx, ny, nz, phi, phi_next, sigma, eps, dt, 1);
+    if (st) return st;
+    std::lock_guard<std::mutex> lk(c->mu);
+    return run(c, volume, vt, nx, ny, nz, phi, phi_next, stages, sigma, eps, lambda1, lambda2, nu, mu, dt, 1);
+}
+
+// ----------------------------------------------------------- kernel timing
+
+extern "C" rsf_status rsf_prof_enable(rsf_ctx *c, int32_t on) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    RSF_CUDA(cudaSetDevice(c->device));
+    RSF_CUDA(cudaStreamSynchronize(c->stream));
+    c->prof.on = on != 0;
+    if (on) c->prof.reset();
+    return RSF_OK;
+}
+
+extern "C" int32_t rsf_prof_count(void) { return rsf::KID_COUNT; }
+
+extern "C" const char *rsf_prof_name(int32_t k) { return rsf::kernel_name(k); }
+
+extern "C" rsf_status rsf_prof_get(rsf_ctx *c, int32_t k, int64_t *launches, double *total_ms) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    if (k < 0 || k >= rsf::KID_COUNT) return fail(RSF_E_INVAL, "unknown kernel index %d", (int)k);
+    std::lock_guard<std::mutex> lk(c->mu);
+    RSF_CUDA(cudaSetDevice(c->device));
+    RSF_CUDA(cudaStreamSynchronize(c->stream));
+    int64_t cnt = 0;
+    double ms = 0.0;
+    for (const auto &r : c->prof.recs) {
+        if (r.id != k) continue;
+        float t = 0.f;
+        RSF_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+        ms += t;
+        ++cnt;
+    }
+    if (launches) *launches = cnt;
+    if (total_ms) *total_ms = ms;
+    return RSF_OK;
+}

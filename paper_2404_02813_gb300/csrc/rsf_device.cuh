@@ -1,0 +1,58 @@
+// rsf_device.cuh -- device-side building blocks of the RSF level-set update
+// (arXiv 2404.02813, Sec. 3): the Heaviside and Dirac functions, the
+// reflect-101 boundary map of the finite differences, and the parameter
+// blocks every kernel receives by value.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rsf {
+
+constexpr int RMAX = 16;                 // largest supported kernel radius (sigma <= 8)
+constexpr float INV_PI = 0.318309886183790671538f;
+
+// Normalised discrete Gaussian taps of Eq. (7), g[k + R] for k = -R..R.
+struct Taps {
+    int R;
+    float g[2 * RMAX + 1];
+};
+
+// Volume shape, x fastest.
+struct Dims {
+    int nx, ny, nz;
+    long long plane;  // nx * ny
+    long long n;      // nx * ny * nz
+};
+
+// Scalars of the update, Eqs. (1), (13), (14).
+struct Coeffs {
+    float eps, lambda1, lambda2, nu, mu, dt;
+};
+
+// Eq. (10), H = 1/2 + atan(u/eps)/pi, evaluated without cancellation on the
+// small side: for u < 0, H = atan(eps/|u|)/pi; for u >= 0, H = 1 - atan(eps/u)/pi.
+// (u = 0 gives eps/0 = inf, atan(inf) = pi/2, H = 1/2.)
+__device__ __forceinline__ float heaviside(float u, float eps) {
+    float r = atanf(eps / fabsf(u)) * INV_PI;
+    return u < 0.f ? r : 1.f - r;
+}
+
+// 1 - H for the same u, also without cancellation on its small side.
+__device__ __forceinline__ float heaviside_c(float u, float eps) {
+    float r = atanf(eps / fabsf(u)) * INV_PI;
+    return u < 0.f ? 1.f - r : r;
+}
+
+// Eq. (14), delta = (eps/pi) / (eps^2 + u^2).
+__device__ __forceinline__ float dirac(float u, float eps) {
+    return (eps * INV_PI) / (eps * eps + u * u);
+}
+
+// Reflect-101 index map onto [0, n): -1 -> 1, n -> n-2 (needs n >= 2 and |overshoot| < n).
+__device__ __forceinline__ int refl101(int i, int n) {
+    i = i < 0 ? -i : i;
+    return i >= n ? 2 * (n - 1) - i : i;
+}
+
+}  // namespace rsf

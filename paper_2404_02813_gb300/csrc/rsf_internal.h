@@ -1,0 +1,75 @@
+// rsf_internal.h -- host-side interfaces between the C ABI layer and the
+// kernel translation units of librsf.so.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "rsf_device.cuh"
+
+namespace rsf {
+
+// Kernel identifiers for the per-launch timing of rsf_prof_*.
+enum KernelId {
+    KID_AX = 0,    // group A, x pass: H products + x convolution
+    KID_AY,        // group A, y pass
+    KID_AZ,        // group A, z pass + local fits epilogue
+    KID_BX,        // group B, x pass
+    KID_BY,        // group B, y pass
+    KID_BZ,        // group B, z pass + data term, curvature and update epilogue
+    KID_COUNT
+};
+const char *kernel_name(int id);
+
+// Records CUDA event pairs around launches while enabled.
+struct Profiler {
+    bool on = false;
+    cudaStream_t stream = nullptr;
+    struct Rec { int id; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    int open_id = -1;
+    cudaEvent_t open_a = nullptr;
+
+    cudaEvent_t take();
+    void begin(int id);
+    void end();
+    void reset();
+    void release();
+};
+
+// RAII bracket around one launch.
+struct ProfScope {
+    Profiler *p;
+    ProfScope(Profiler *prof, int id) : p(prof && prof->on ? prof : nullptr) { if (p) p->begin(id); }
+    ~ProfScope() { if (p) p->end(); }
+};
+
+// Device fields of one volume (all FP32, n elements unless noted).
+struct Fields {
+    Dims d{};
+    float *I = nullptr;       // centred, scaled image  (I - m) / s
+    float *KI = nullptr;      // K * (centred image)
+    float *prof = nullptr;    // zero-padding profiles p_x[nx], p_y[ny], p_z[nz]; K*1 = p_x p_y p_z
+    float *cs = nullptr;      // [0] m, [1] 1/s, [2] s^2   (centring constants)
+    float *partials = nullptr;// reduction scratch, 3 * kStatBlocks floats
+    float *phi[2] = {nullptr, nullptr};
+    float *t[6] = {};         // stage buffers of the pass path
+};
+
+constexpr int kStatBlocks = 1024;
+
+// Set-up: centring constants, centred image, K*I and the K*1 profiles.
+// `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
+cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s);
+
+// One iteration of the separable pass path: phi_in -> phi_out.
+// `stages`, when not null, receives RSF_NSTAGES fields (f1, f2, g, kappa, L).
+cudaError_t iterate_passes(const Taps &taps, const Coeffs &c, Fields &f, const float *phi_in, float *phi_out,
+                           float *stages, Profiler *prof, cudaStream_t s);
+
+}  // namespace rsf

@@ -1,0 +1,218 @@
+"""Python binding of librsf.so (include/rsf.h): argument marshalling only.
+
+Every step of the level-set iteration runs in the library's CUDA kernels;
+this module passes pointers, sizes and scalars through ctypes.  Arrays may be
+torch tensors (CUDA or CPU) or numpy arrays; volumes are [nz, ny, nx], x
+fastest.  If the library has not been built, every call raises -- there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Dict, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librsf.so")
+
+RSF_OK, RSF_PENDING = 0, 1
+STATUS_NAMES = {0: "RSF_OK", 1: "RSF_PENDING", -1: "RSF_E_INVAL", -2: "RSF_E_NOMEM", -3: "RSF_E_CUDA",
+                -4: "RSF_E_TIMEOUT", -5: "RSF_E_NOTFOUND", -6: "RSF_E_BUSY", -7: "RSF_E_CANCELLED"}
+RSF_U8, RSF_U16, RSF_F32 = 0, 1, 2
+STAGES = ("f1", "f2", "g", "kappa", "lap")
+
+EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
+            "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error")
+
+
+class RSFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load librsf.so and declare its signatures. Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librsf.so is not built ({path}); run __graft_entry__.build() first")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+    L.rsf_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32]
+    L.rsf_create.restype = i32
+    L.rsf_destroy.argtypes = [vp]
+    L.rsf_destroy.restype = None
+    L.rsf_stream.argtypes = [vp]
+    L.rsf_stream.restype = vp
+    L.rsf_evolve.argtypes = [vp, vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32]
+    L.rsf_evolve.restype = i32
+    L.rsf_step_stages.argtypes = [vp, vp, i32, i64, i64, i64, vp, vp, vp, f32, f32, f32, f32, f32, f32, f32]
+    L.rsf_step_stages.restype = i32
+    L.rsf_prof_enable.argtypes = [vp, i32]
+    L.rsf_prof_enable.restype = i32
+    L.rsf_prof_count.argtypes = []
+    L.rsf_prof_count.restype = i32
+    L.rsf_prof_name.argtypes = [i32]
+    L.rsf_prof_name.restype = ctypes.c_char_p
+    L.rsf_prof_get.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
+    L.rsf_prof_get.restype = i32
+    L.rsf_last_error.argtypes = []
+    L.rsf_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(st: int):
+    if st < 0:
+        raise RSFError(st, load_library().rsf_last_error().decode())
+    return st
+
+
+def _ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _vol_dtype(a) -> int:
+    name = str(a.dtype).replace("torch.", "")
+    if name == "uint8":
+        return RSF_U8
+    if name == "uint16":
+        return RSF_U16
+    if name == "float32":
+        return RSF_F32
+    raise TypeError(f"volume dtype must be uint8, uint16 or float32, not {name}")
+
+
+def _shape(a):
+    s = tuple(a.shape)
+    if len(s) != 3:
+        raise ValueError("expected a 3-D [nz, ny, nx] array")
+    return s
+
+
+@dataclass
+class Params:
+    """Scalars of the update (Eqs. 1, 6, 10-14)."""
+    sigma: float = 3.0
+    eps: float = 1.0
+    lambda1: float = 1.0
+    lambda2: float = 2.0
+    nu: float = 0.004 * 255.0 ** 2
+    mu: float = 1.0
+    dt: float = 0.1
+
+    @classmethod
+    def of(cls, p) -> "Params":
+        if isinstance(p, Params):
+            return p
+        return cls(**{k: float(p[k]) for k in ("sigma", "eps", "lambda1", "lambda2", "nu", "mu", "dt")})
+
+    def tuple(self):
+        return (self.sigma, self.eps, self.lambda1, self.lambda2, self.nu, self.mu, self.dt)
+
+
+class Context:
+    """One rsf_ctx: a device, an HBM budget and a CUDA stream."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        L = load_library()
+        h = ctypes.c_void_p()
+        _check(L.rsf_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), 0))
+        self._h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load_library().rsf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def stream_handle(self) -> int:
+        return int(load_library().rsf_stream(self._h) or 0)
+
+    def evolve(self, volume, phi0, params, iters: int, out=None):
+        """Run `iters` iterations from phi0; returns `out` (allocated like phi0 if None)."""
+        p = Params.of(params)
+        nz, ny, nx = _shape(volume)
+        if _shape(phi0) != (nz, ny, nx):
+            raise ValueError("volume and phi0 shapes differ")
+        if str(phi0.dtype).replace("torch.", "") != "float32":
+            raise TypeError("phi0 must be float32")
+        if out is None:
+            out = phi0.clone() if hasattr(phi0, "clone") else np.empty_like(phi0)
+        _check(load_library().rsf_evolve(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0),
+                                         _ptr(out), *p.tuple(), int(iters)))
+        return out
+
+    def step_stages(self, volume, phi, params, phi_next=None, stages=None):
+        """One iteration with the stage fields; returns (phi_next, stages[5, nz, ny, nx])."""
+        p = Params.of(params)
+        nz, ny, nx = _shape(volume)
+        if phi_next is None:
+            phi_next = phi.clone() if hasattr(phi, "clone") else np.empty_like(phi)
+        if stages is None:
+            if hasattr(phi, "new_empty"):
+                stages = phi.new_empty((len(STAGES), nz, ny, nx))
+            else:
+                stages = np.empty((len(STAGES), nz, ny, nx), dtype=np.float32)
+        _check(load_library().rsf_step_stages(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi),
+                                              _ptr(phi_next), _ptr(stages), *p.tuple()))
+        return phi_next, stages
+
+    # kernel timing ---------------------------------------------------------
+    def prof_enable(self, on: bool = True):
+        _check(load_library().rsf_prof_enable(self._h, 1 if on else 0))
+
+    def prof_get(self) -> Dict[str, tuple]:
+        L = load_library()
+        out = {}
+        for k in range(L.rsf_prof_count()):
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            _check(L.rsf_prof_get(self._h, k, ctypes.byref(n), ctypes.byref(ms)))
+            out[L.rsf_prof_name(k).decode()] = (int(n.value), float(ms.value))
+        return out
+
+
+_default: Dict[int, Context] = {}
+
+
+def context(device: int = 0) -> Context:
+    if device not in _default:
+        _default[device] = Context(device)
+    return _default[device]
+
+
+def evolve(volume, phi0, sigma=3.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * 255.0 ** 2, mu=1.0, dt=0.1,
+           iters=50, out=None, device: Optional[int] = None):
+    """rsf_evolve on the default context of `device` (the tensor's device, else 0)."""
+    if device is None:
+        device = volume.device.index if getattr(volume, "is_cuda", False) else 0
+    p = Params(sigma, eps, lambda1, lambda2, nu, mu, dt)
+    return context(device).evolve(volume, phi0, p, iters, out=out)

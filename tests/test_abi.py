@@ -1,0 +1,67 @@
+"""CPU-side checks of the C ABI: librsf.so builds, loads, exports every
+function include/rsf.h declares, and reports errors without a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rsf_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2404_02813_gb300 import build, rsf
+    build.build()
+    return rsf.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("rsf_create", "rsf_destroy", "rsf_evolve", "rsf_last_error", "rsf_step_stages"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(os.path.join(ROOT, "paper_2404_02813_gb300", "librsf.so"))
+    missing = [n for n in sorted(_declared()) if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_binding_lists_every_declared_symbol():
+    from paper_2404_02813_gb300 import rsf
+    assert set(rsf.EXPORTED) >= _declared() - {"rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel"}
+
+
+def test_null_context_is_invalid_argument(lib):
+    st = lib.rsf_evolve(None, None, 0, 4, 4, 4, None, None, 3.0, 1.0, 1.0, 2.0, 1.0, 1.0, 0.1, 1)
+    assert st == -1
+    assert b"null context" in lib.rsf_last_error()
+
+
+def test_create_reports_errors_without_aborting(lib):
+    import torch
+    h = ctypes.c_void_p()
+    st = lib.rsf_create(ctypes.byref(h), 0, 0, 7)   # flags must be 0
+    assert st == -1 and not h.value
+    if not torch.cuda.is_available():
+        st = lib.rsf_create(ctypes.byref(h), 0, 0, 0)
+        assert st == -3 and not h.value
+        assert len(lib.rsf_last_error()) > 0
+
+
+def test_prof_names(lib):
+    n = lib.rsf_prof_count()
+    names = [lib.rsf_prof_name(k).decode() for k in range(n)]
+    assert len(set(names)) == n and all(s.startswith("rsf_") for s in names)
+    assert lib.rsf_prof_name(n) is None
