@@ -130,6 +130,35 @@ int32_t rsf_prof_count(void);
 const char *rsf_prof_name(int32_t kernel);
 rsf_status rsf_prof_get(rsf_ctx *ctx, int32_t kernel, int64_t *launches, double *total_ms);
 
+/*
+ * rsf_evolve_noalloc -- rsf_evolve for small volumes without any device
+ * allocation.  The paper has no counterpart; this entry exists for callers
+ * that may not allocate GPU memory while they run: a plug-in whose host
+ * application owns all device memory through its own pool, a streaming or
+ * real-time thread that cannot afford the device-wide synchronisation a
+ * cudaMalloc / cudaFree may cause, or a service whose memory was sized once
+ * at start-up.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   volume, phi0, phi_out  DEVICE pointers of the current device (host
+ *            pointers are rejected with RSF_E_INVAL); phi_out may alias phi0.
+ *   stream   the cudaStream_t (as void*) the work is queued on; NULL is the
+ *            legacy default stream.
+ *   other arguments as rsf_evolve.
+ * Working fields live in one static device array built into the library
+ * (about 10.5 MB, held by every GPU that loads librsf.so until the process
+ * exits), which limits the volume to nx*ny*nz <= 262144 voxels (e.g. 64^3);
+ * larger volumes are rejected with RSF_E_INVAL.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Asynchronous:
+ * returns once the work is queued; phi_out is ready when `stream` reaches it.
+ * All calls on a device share the array and it keeps the last call's
+ * contents (nothing in it needs to start at zero); calls whose work overlaps
+ * on the GPU race on it and must be serialised by the caller.
+ * Errors: RSF_E_INVAL (arguments, size limit), RSF_E_CUDA (launch failures).
+ */
+rsf_status rsf_evolve_noalloc(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                              const float *phi0, float *phi_out, float sigma, float eps, float lambda1,
+                              float lambda2, float nu, float mu, float dt, int32_t iters, void *stream);
+
 /* Thread-local description of the last error returned on this thread. */
 const char *rsf_last_error(void);
 

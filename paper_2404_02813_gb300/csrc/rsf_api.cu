@@ -40,6 +40,10 @@ static rsf_status cuda_fail(cudaError_t e, const char *what) {
 
 extern "C" const char *rsf_last_error(void) { return g_last_error.c_str(); }
 
+namespace rsf {
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace rsf
+
 // ---------------------------------------------------------------- profiler
 
 namespace rsf {
@@ -126,7 +130,7 @@ static void dev_free(rsf_ctx *c, void *p, size_t bytes) {
     c->used -= std::min<uint64_t>(c->used, bytes);
 }
 
-static constexpr int kBigFields = 11;  // I, phi[2], t[8]
+static constexpr int kBigFields = 3 + (int)(sizeof(rsf::Fields::t) / sizeof(float *));  // I, phi[2], t[]
 
 static void free_fields(rsf_ctx *c) {
     size_t fb = sizeof(float) * (size_t)c->cap_n;
@@ -255,10 +259,11 @@ extern "C" rsf_status rsf_create(rsf_ctx **out, int device, uint64_t hbm_budget_
     rsf_ctx *c = new rsf_ctx();
     c->device = device;
     c->budget = hbm_budget_bytes ? hbm_budget_bytes : (uint64_t)(0.9 * (double)fr);
-    cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    // a blocking stream: ordered after work the caller queued on the legacy default stream
+    cudaError_t e = cudaStreamCreate(&c->stream);
     if (e != cudaSuccess) {
         delete c;
-        return cuda_fail(e, "cudaStreamCreateWithFlags");
+        return cuda_fail(e, "cudaStreamCreate");
     }
     c->prof.stream = c->stream;
     *out = c;
@@ -293,6 +298,9 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     if (st) return st;
     rsf::Fields &f = c->f;
     const long long n = f.d.n;
+    bool ready = f.I && f.prof && f.cs && f.partials && f.phi[0] && f.phi[1];
+    for (float *p : f.t) ready = ready && p;
+    if (!ready) return fail(RSF_E_CUDA, "internal error: working fields are not allocated");
     float *dump = nullptr;
     if (stages) {
         if (on_device(stages)) {

@@ -53,19 +53,25 @@ struct ProfScope {
 struct Fields {
     Dims d{};
     float *I = nullptr;       // centred, scaled image  (I - m) / s
-    float *KI = nullptr;      // K * (centred image)
     float *prof = nullptr;    // zero-padding profiles p_x[nx], p_y[ny], p_z[nz]; K*1 = p_x p_y p_z
-    float *cs = nullptr;      // [0] m, [1] 1/s, [2] s^2   (centring constants)
+    float *cs = nullptr;      // [0] m, [1] 1/s, [2] s^2, [3] s   (centring constants)
     float *partials = nullptr;// reduction scratch, 3 * kStatBlocks floats
     float *phi[2] = {nullptr, nullptr};
-    float *t[6] = {};         // stage buffers of the pass path
+    float *t[8] = {};         // stage buffers of the pass path
 };
 
 constexpr int kStatBlocks = 1024;
 
-// Set-up: centring constants, centred image, K*I and the K*1 profiles.
+// Set-up: centring constants, centred image and the K*1 profiles.
 // `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
 cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s);
+
+// The centring half of setup_image alone (statistics and centred image, no
+// profiles); enqueues on `s` and never synchronises.
+cudaError_t centre_image(const void *vol, int vt, Fields &f, cudaStream_t s);
+
+// Sets the calling thread's rsf_last_error() text.
+void set_last_error(const char *msg);
 
 // One iteration of the separable pass path: phi_in -> phi_out.
 // `stages`, when not null, receives RSF_NSTAGES fields (f1, f2, g, kappa, L).

@@ -315,6 +315,23 @@ cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cu
     return cudaGetLastError();
 }
 
+cudaError_t centre_image(const void *vol, int vt, Fields &f, cudaStream_t s) {
+    const Dims &d = f.d;
+    const int eb = 1184;
+    switch (vt) {
+        case 0: k_stats<uint8_t><<<kStatBlocks, 256, 0, s>>>((const uint8_t *)vol, d.n, f.partials); break;
+        case 1: k_stats<uint16_t><<<kStatBlocks, 256, 0, s>>>((const uint16_t *)vol, d.n, f.partials); break;
+        default: k_stats<float><<<kStatBlocks, 256, 0, s>>>((const float *)vol, d.n, f.partials);
+    }
+    k_stats_final<<<1, kStatBlocks, 0, s>>>(f.partials, d.n, f.cs);
+    switch (vt) {
+        case 0: k_center<uint8_t><<<eb, 256, 0, s>>>((const uint8_t *)vol, d.n, f.cs, f.I); break;
+        case 1: k_center<uint16_t><<<eb, 256, 0, s>>>((const uint16_t *)vol, d.n, f.cs, f.I); break;
+        default: k_center<float><<<eb, 256, 0, s>>>((const float *)vol, d.n, f.cs, f.I);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t iterate_passes(const Taps &t, const Coeffs &c, Fields &f, const float *phi_in, float *phi_out,
                            float *stages, Profiler *prof, cudaStream_t s) {
     const Dims &d = f.d;

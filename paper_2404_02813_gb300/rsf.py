@@ -25,7 +25,9 @@ RSF_U8, RSF_U16, RSF_F32 = 0, 1, 2
 STAGES = ("f1", "f2", "g", "kappa", "lap")
 
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
-            "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error")
+            "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc")
+
+NOALLOC_MAX_VOXELS = 1 << 18
 
 
 class RSFError(RuntimeError):
@@ -64,6 +66,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_prof_name.restype = ctypes.c_char_p
     L.rsf_prof_get.argtypes = [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double)]
     L.rsf_prof_get.restype = i32
+    L.rsf_evolve_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, vp]
+    L.rsf_evolve_noalloc.restype = i32
     L.rsf_last_error.argtypes = []
     L.rsf_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -86,6 +90,16 @@ def _ptr(a) -> int:
             raise ValueError("array must be C-contiguous")
         return a.ctypes.data
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _order_after_caller(*arrays):
+    """The library's stream follows the legacy default stream; work the caller
+    queued on another torch stream is finished first."""
+    if any(getattr(a, "is_cuda", False) for a in arrays):
+        import torch
+        cur = torch.cuda.current_stream()
+        if cur != torch.cuda.default_stream():
+            cur.synchronize()
 
 
 def _vol_dtype(a) -> int:
@@ -166,6 +180,7 @@ class Context:
             raise TypeError("phi0 must be float32")
         if out is None:
             out = phi0.clone() if hasattr(phi0, "clone") else np.empty_like(phi0)
+        _order_after_caller(volume, phi0, out)
         _check(load_library().rsf_evolve(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0),
                                          _ptr(out), *p.tuple(), int(iters)))
         return out
@@ -181,6 +196,7 @@ class Context:
                 stages = phi.new_empty((len(STAGES), nz, ny, nx))
             else:
                 stages = np.empty((len(STAGES), nz, ny, nx), dtype=np.float32)
+        _order_after_caller(volume, phi, phi_next, stages)
         _check(load_library().rsf_step_stages(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi),
                                               _ptr(phi_next), _ptr(stages), *p.tuple()))
         return phi_next, stages
@@ -216,3 +232,23 @@ def evolve(volume, phi0, sigma=3.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 
         device = volume.device.index if getattr(volume, "is_cuda", False) else 0
     p = Params(sigma, eps, lambda1, lambda2, nu, mu, dt)
     return context(device).evolve(volume, phi0, p, iters, out=out)
+
+
+def evolve_noalloc(volume, phi0, params, iters: int, out, stream=None):
+    """rsf_evolve_noalloc: the evolution for volumes of at most 262144 voxels
+    without any device allocation, for callers that must not allocate GPU
+    memory (their device memory belongs to a pool they do not control, or an
+    allocation's implicit synchronisation is not acceptable).  `volume`,
+    `phi0` and `out` must be CUDA tensors; the work is queued on `stream`
+    (a torch.cuda.Stream, default the current stream) and is complete when that
+    stream is.  Overlapping calls race on the library's shared static scratch.
+    """
+    import torch
+    p = Params.of(params)
+    nz, ny, nx = _shape(volume)
+    if _shape(phi0) != (nz, ny, nx) or _shape(out) != (nz, ny, nx):
+        raise ValueError("volume, phi0 and out shapes differ")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(load_library().rsf_evolve_noalloc(_ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0), _ptr(out),
+                                             *p.tuple(), int(iters), int(s.cuda_stream)))
+    return out
