@@ -34,13 +34,20 @@ sys.path.insert(0, ROOT)
 # Algorithmic HBM bytes per voxel and launch of each per-iteration kernel: the
 # fields it must read once and write once (FP32), independent of tiling.
 ALGO_BYTES_PER_VOXEL = {
+    # six-pass schedule
     "rsf_a_x": 4 + 4 + 16,   # phi, I -> four H-product fields
     "rsf_a_y": 16 + 16,
     "rsf_a_z": 16 + 8,       # four fields -> a, b
     "rsf_b_x": 8 + 8,
     "rsf_b_y": 8 + 8,
     "rsf_b_z": 8 + 4 + 4 + 4,  # a, b, I, phi -> phi'
+    # tiled schedule
+    "rsf_ta_xy": 4 + 4 + 16,   # phi, I -> float4 of x/y-convolved H products
+    "rsf_ta_z": 16 + 8,        # float4 -> (a, b)
+    "rsf_tb_xy": 8 + 8,        # (a, b) -> x/y-convolved (a, b)
+    "rsf_tb_z": 8 + 4 + 4 + 4 + 4,  # (a, b), I, phi -> phi', q(phi')
 }
+SETUP_LAUNCHES = 3  # statistics, their reduction, centring
 
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
@@ -50,9 +57,9 @@ NCU_TRAFFIC = {}
 P_LIGHTSHEET = 4300.0
 
 
-def _kernel_source_sha() -> str:
-    p = os.path.join(ROOT, "paper_2404_02813_gb300", "csrc", "rsf_passes.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+def _source_sha(fname: str) -> str:
+    p = os.path.join(ROOT, "paper_2404_02813_gb300", "csrc", fname)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else ""
 
 
 def peaks():
@@ -114,14 +121,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, size=None, iters_override=None):
     from paper_2404_02813_gb300 import synth
+    e = size or 512
     if name == "lightsheet512":
-        vol = synth.lightsheet_volume_u16((512, 512, 512), brick=rank)
+        vol = synth.lightsheet_volume_u16((e, e, e), brick=rank)
         params = dict(sigma=3.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P_LIGHTSHEET ** 2, mu=1.0, dt=0.1)
         iters = 200
     elif name == "lightsheet512_s5":
-        vol = synth.lightsheet_volume_u16((512, 512, 512), brick=rank)
+        vol = synth.lightsheet_volume_u16((e, e, e), brick=rank)
         params = dict(sigma=5.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P_LIGHTSHEET ** 2, mu=1.0, dt=0.1)
         iters = 200
     elif name == "tree64":
@@ -131,7 +139,7 @@ def make_workload(name: str, rank: int):
     else:
         raise SystemExit(f"unknown workload {name}")
     phi0 = synth.box_phi0(vol.shape, 32) if name == "tree64" else synth.mean_rule_phi0(vol)
-    return vol, phi0, params, iters
+    return vol, phi0, params, iters_override or iters
 
 
 def workload_desc(name, vol, params, iters):
@@ -165,7 +173,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     import oracle
-    vol, phi0, params, iters = make_workload(args.workload, 0)
+    vol, phi0, params, iters = make_workload(args.workload, 0, args.size, args.iters)
     c = 48
     I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
     ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
@@ -199,6 +207,9 @@ def main():
     ap.add_argument("--workload", default="lightsheet512", choices=["lightsheet512", "lightsheet512_s5", "tree64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=None, help="cube edge instead of the workload's (profiling runs)")
+    ap.add_argument("--iters", type=int, default=None, help="iterations per step instead of the workload's")
+    ap.add_argument("--path", default="auto", choices=["auto", "passes", "tiled"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "rsf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -222,12 +233,13 @@ def main():
         if world > 1:
             dist.barrier()
 
-    vol, phi0, params, iters = make_workload(args.workload, rank)
+    vol, phi0, params, iters = make_workload(args.workload, rank, args.size, args.iters)
     n_vox = vol.size
     v = torch.from_numpy(vol).cuda()
     ph0 = torch.from_numpy(phi0).cuda()
     out = torch.empty_like(ph0)
     ctx = rsf.Context(local)
+    ctx.set_path(args.path)
     stream = torch.cuda.ExternalStream(ctx.stream_handle)
 
     for _ in range(args.warmup):
@@ -286,10 +298,10 @@ def main():
         avg_s = tot_ms / max(n_l, 1) / 1e3
         algo = ALGO_BYTES_PER_VOXEL[dom] * n_vox
         achieved = algo / avg_s / 1e9
-        sha = _kernel_source_sha()
         tr = NCU_TRAFFIC.get(dom)
-        traffic = tr["bytes_per_voxel"] * n_vox if tr and tr.get("source_sha") == sha else None
-        launches_per_step = 3 + len(ALGO_BYTES_PER_VOXEL) * iters
+        traffic = (tr["bytes_per_voxel"] * n_vox
+                   if tr and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
+        launches = SETUP_LAUNCHES * args.steps + sum(n for n, _ in prof.values())
         line = {
             "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -304,7 +316,7 @@ def main():
             "kernels": {k: {"launches": n, "ms": round(m, 3), "share": round(m / max(sum(x[1] for x in prof.values()), 1e-9), 4)}
                         for k, (n, m) in prof.items() if n},
             "clocks": clk,
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches,
             "e2e": e2e,
         }
         if world == 1 and not args.no_cpu_baseline:

@@ -90,7 +90,7 @@ void *rsf_stream(rsf_ctx *ctx);
  *   mu       weight of the regulariser L phi - kappa.
  *   dt       time step (> 0).
  *   iters    number of iterations (>= 0; 0 copies phi0 to phi_out).
- * Set-up work (centring of I, K*I, the K*1 profiles) runs once per call.
+ * Set-up work (centring of I, the K*1 profiles) runs once per call.
  * Errors: RSF_E_INVAL, RSF_E_NOMEM, RSF_E_CUDA.
  */
 rsf_status rsf_evolve(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
@@ -117,6 +117,25 @@ typedef enum {
 rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
                            const float *phi, float *phi_next, float *stages, float sigma, float eps,
                            float lambda1, float lambda2, float nu, float mu, float dt);
+
+/*
+ * rsf_set_option -- per-context settings of the iteration schedule.
+ *   RSF_OPT_PATH    RSF_PATH_AUTO (default): the tiled four-kernel iteration
+ *                   where it has kernels for the radius R (2-6, 8, 10, 12),
+ *                   else the six-pass iteration; RSF_PATH_PASSES: always the
+ *                   six-pass iteration; RSF_PATH_TILED: the tiled iteration
+ *                   (other radii then fail with RSF_E_INVAL).
+ *   RSF_OPT_ZCHUNK  z planes per CTA of the z-marching kernels; 0 (default)
+ *                   picks enough chunks for about 16 CTAs per SM; else >= 8.
+ * Both give the same arithmetic per voxel up to the order of FP32 rounding.
+ * Errors: RSF_E_INVAL (unknown key or value).
+ */
+#define RSF_OPT_PATH 1
+#define RSF_OPT_ZCHUNK 2
+#define RSF_PATH_AUTO 0
+#define RSF_PATH_PASSES 1
+#define RSF_PATH_TILED 2
+rsf_status rsf_set_option(rsf_ctx *ctx, int32_t key, int64_t value);
 
 /*
  * Kernel timing.  While enabled, the context records a CUDA event pair on its

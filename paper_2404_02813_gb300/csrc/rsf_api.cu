@@ -49,7 +49,8 @@ void set_last_error(const char *msg) { g_last_error = msg; }
 namespace rsf {
 
 const char *kernel_name(int id) {
-    static const char *names[KID_COUNT] = {"rsf_a_x", "rsf_a_y", "rsf_a_z", "rsf_b_x", "rsf_b_y", "rsf_b_z"};
+    static const char *names[KID_COUNT] = {"rsf_a_x",  "rsf_a_y",    "rsf_a_z",  "rsf_b_x",   "rsf_b_y",
+                                           "rsf_b_z",  "rsf_ta_xy",  "rsf_ta_z", "rsf_tb_xy", "rsf_tb_z"};
     return (id >= 0 && id < KID_COUNT) ? names[id] : nullptr;
 }
 
@@ -102,12 +103,15 @@ struct rsf_ctx {
 
     rsf::Fields f;
     long long cap_n = 0;     // elements per big field currently allocated
+    long long cap_np = 0;    // elements per stage field (pitched) currently allocated
     long long cap_prof = 0;  // profile floats allocated
     void *staging = nullptr; // device copy of a host volume
     size_t staging_cap = 0;
     float *dump = nullptr;   // device stage dump for host destinations
     size_t dump_cap = 0;
     rsf::Profiler prof;
+    int opt_path = RSF_PATH_AUTO;
+    int opt_zchunk = 0;
 };
 
 static rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
@@ -130,15 +134,17 @@ static void dev_free(rsf_ctx *c, void *p, size_t bytes) {
     c->used -= std::min<uint64_t>(c->used, bytes);
 }
 
-static constexpr int kBigFields = 3 + (int)(sizeof(rsf::Fields::t) / sizeof(float *));  // I, phi[2], t[]
 
 static void free_fields(rsf_ctx *c) {
     size_t fb = sizeof(float) * (size_t)c->cap_n;
     dev_free(c, c->f.I, fb);
     for (float *&p : c->f.phi) { dev_free(c, p, fb); p = nullptr; }
-    for (float *&p : c->f.t) { dev_free(c, p, fb); p = nullptr; }
+    for (float *&p : c->f.q) { dev_free(c, p, fb); p = nullptr; }
+    dev_free(c, c->f.t[0], sizeof(float) * 8 * (size_t)c->cap_np);
+    for (float *&p : c->f.t) p = nullptr;
     c->f.I = nullptr;
     c->cap_n = 0;
+    c->cap_np = 0;
     dev_free(c, c->f.prof, sizeof(float) * (size_t)c->cap_prof);
     c->f.prof = nullptr;
     c->cap_prof = 0;
@@ -146,36 +152,46 @@ static void free_fields(rsf_ctx *c) {
 
 static rsf_status ensure_fields(rsf_ctx *c, int nx, int ny, int nz) {
     rsf::Dims d{nx, ny, nz, (long long)nx * ny, (long long)nx * ny * nz};
-    if (d.n > c->cap_n) {
+    const int px = rsf::tiled_pitch(nx);
+    const long long np = (long long)px * ny * nz;  // >= n: also holds the pass path's fields
+    if (d.n > c->cap_n || np > c->cap_np) {
         free_fields(c);
-        size_t fb = sizeof(float) * (size_t)d.n;
-        if ((uint64_t)kBigFields * fb + c->used > c->budget)
+        const size_t fb = sizeof(float) * (size_t)d.n;
+        const size_t need = 5 * fb + sizeof(float) * 8 * (size_t)np;
+        if (need + c->used > c->budget)
             return fail(RSF_E_NOMEM, "volume of %lld voxels needs %llu bytes of working fields; budget %llu, in use %llu",
-                        d.n, (unsigned long long)kBigFields * fb, (unsigned long long)c->budget,
-                        (unsigned long long)c->used);
+                        d.n, (unsigned long long)need, (unsigned long long)c->budget, (unsigned long long)c->used);
         rsf_status st;
         if ((st = dev_alloc(c, (void **)&c->f.I, fb))) return st;
         for (float *&p : c->f.phi)
             if ((st = dev_alloc(c, (void **)&p, fb))) return st;
-        for (float *&p : c->f.t)
+        for (float *&p : c->f.q)
             if ((st = dev_alloc(c, (void **)&p, fb))) return st;
+        if ((st = dev_alloc(c, (void **)&c->f.t[0], sizeof(float) * 8 * (size_t)np))) return st;
+        for (int i = 1; i < 8; ++i) c->f.t[i] = c->f.t[0] + (size_t)i * np;
         c->cap_n = d.n;
+        c->cap_np = np;
+    } else {
+        for (int i = 1; i < 8; ++i) c->f.t[i] = c->f.t[0] + (size_t)i * c->cap_np;
     }
-    long long np = (long long)nx + ny + nz;
-    if (np > c->cap_prof) {
+    long long npf = (long long)nx + ny + nz;
+    if (npf > c->cap_prof) {
         dev_free(c, c->f.prof, sizeof(float) * (size_t)c->cap_prof);
         c->f.prof = nullptr;
-        rsf_status st = dev_alloc(c, (void **)&c->f.prof, sizeof(float) * np);
+        rsf_status st = dev_alloc(c, (void **)&c->f.prof, sizeof(float) * npf);
         if (st) return st;
-        c->cap_prof = np;
+        c->cap_prof = npf;
     }
     if (!c->f.cs) {
         rsf_status st = dev_alloc(c, (void **)&c->f.cs, sizeof(float) * 4);
         if (st) return st;
         st = dev_alloc(c, (void **)&c->f.partials, sizeof(float) * 3 * rsf::kStatBlocks);
         if (st) return st;
+        st = dev_alloc(c, (void **)&c->f.err, sizeof(int));
+        if (st) return st;
     }
     c->f.d = d;
+    c->f.px = px;
     return RSF_OK;
 }
 
@@ -279,6 +295,7 @@ extern "C" void rsf_destroy(rsf_ctx *c) {
         free_fields(c);
         dev_free(c, c->f.cs, sizeof(float) * 4);
         dev_free(c, c->f.partials, sizeof(float) * 3 * rsf::kStatBlocks);
+        dev_free(c, c->f.err, sizeof(int));
         dev_free(c, c->staging, c->staging_cap);
         dev_free(c, c->dump, c->dump_cap);
         c->prof.release();
@@ -298,7 +315,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     if (st) return st;
     rsf::Fields &f = c->f;
     const long long n = f.d.n;
-    bool ready = f.I && f.prof && f.cs && f.partials && f.phi[0] && f.phi[1];
+    bool ready = f.I && f.prof && f.cs && f.partials && f.err && f.phi[0] && f.phi[1] && f.q[0] && f.q[1];
     for (float *p : f.t) ready = ready && p;
     if (!ready) return fail(RSF_E_CUDA, "internal error: working fields are not allocated");
     float *dump = nullptr;
@@ -323,17 +340,40 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     const rsf::Coeffs co{eps, lambda1, lambda2, nu, mu, dt};
     RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream));
     RSF_CUDA(cudaMemcpyAsync(f.phi[0], phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    const bool tiled = c->opt_path != RSF_PATH_PASSES && rsf::tiled_supports(taps.R);
+    if (c->opt_path == RSF_PATH_TILED && !tiled)
+        return fail(RSF_E_INVAL, "the tiled path has no kernels for radius %d", taps.R);
+    int zc = c->opt_zchunk;
+    if (tiled) {
+        RSF_CUDA(rsf::tiled_prepare(taps.R));
+        if (zc <= 0) {  // enough z chunks for about 16 CTAs per SM
+            int sms = 0;
+            RSF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+            const long long nxy = (long long)((nx + 31) / 32) * ((ny + 7) / 8);
+            const long long chunks = std::max<long long>(1, (16LL * sms + nxy - 1) / nxy);
+            zc = (int)std::max<long long>(16, (nz + chunks - 1) / chunks);
+        }
+    }
+    RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
+    if (tiled && iters > 0) RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
     int cur = 0;
     for (int it = 0; it < iters; ++it) {
-        cudaError_t e = rsf::iterate_passes(taps, co, f, f.phi[cur], f.phi[cur ^ 1], it == iters - 1 ? dump : nullptr,
-                                            &c->prof, c->stream);
+        float *d_it = it == iters - 1 ? dump : nullptr;
+        cudaError_t e = tiled ? rsf::iterate_tiled(taps, co, f, f.phi[cur], f.q[cur], f.phi[cur ^ 1], f.q[cur ^ 1], d_it,
+                                                   &c->prof, c->stream, zc)
+                              : rsf::iterate_passes(taps, co, f, f.phi[cur], f.phi[cur ^ 1], d_it, &c->prof, c->stream);
         if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
         cur ^= 1;
     }
     RSF_CUDA(cudaMemcpyAsync(phi_out, f.phi[cur], sizeof(float) * n, cudaMemcpyDefault, c->stream));
     if (stages && dump != stages)
         RSF_CUDA(cudaMemcpyAsync(stages, dump, sizeof(float) * n * RSF_NSTAGES, cudaMemcpyDefault, c->stream));
+    int err_word = 0;
+    RSF_CUDA(cudaMemcpyAsync(&err_word, f.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RSF_CUDA(cudaStreamSynchronize(c->stream));
+    if (err_word == rsf::kErrTimeout)
+        return fail(RSF_E_TIMEOUT, "a bounded wait in a pipelined kernel expired; phi_out is not valid");
+    if (err_word != 0) return fail(RSF_E_CUDA, "kernel error word %d", err_word);
     return RSF_OK;
 }
 
@@ -356,6 +396,26 @@ extern "C" rsf_status rsf_step_stages(rsf_ctx *c, const void *volume, rsf_dtype 
     if (st) return st;
     std::lock_guard<std::mutex> lk(c->mu);
     return run(c, volume, vt, nx, ny, nz, phi, phi_next, stages, sigma, eps, lambda1, lambda2, nu, mu, dt, 1);
+}
+
+// ----------------------------------------------------------------- options
+
+extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    switch (key) {
+        case RSF_OPT_PATH:
+            if (value < RSF_PATH_AUTO || value > RSF_PATH_TILED) return fail(RSF_E_INVAL, "unknown path %lld", (long long)value);
+            c->opt_path = (int)value;
+            return RSF_OK;
+        case RSF_OPT_ZCHUNK:
+            if (value < 0 || value > (1 << 20)) return fail(RSF_E_INVAL, "z chunk must lie in [0, 2^20]");
+            if (value != 0 && value < 8) return fail(RSF_E_INVAL, "z chunk must be 0 (automatic) or >= 8");
+            c->opt_zchunk = (int)value;
+            return RSF_OK;
+        default:
+            return fail(RSF_E_INVAL, "unknown option key %d", (int)key);
+    }
 }
 
 // ----------------------------------------------------------- kernel timing

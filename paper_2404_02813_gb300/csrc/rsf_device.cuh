@@ -44,6 +44,28 @@ __device__ __forceinline__ float heaviside_c(float u, float eps) {
     return u < 0.f ? 1.f - r : r;
 }
 
+// The small side of Eq. (10), r = atan(eps/|u|)/pi in (0, 1/2], carrying the
+// sign of u: H = -q for q < 0, else 1 - q; 1 - H = 1 + q for q < 0, else q.
+// These give exactly heaviside() and heaviside_c() of the same u.
+__device__ __forceinline__ float heaviside_q(float u, float eps) {
+    return copysignf(atanf(eps / fabsf(u)) * INV_PI, u);
+}
+__device__ __forceinline__ float h_of_q(float q) { return q < 0.f ? -q : 1.f - q; }
+__device__ __forceinline__ float hc_of_q(float q) { return q < 0.f ? 1.f + q : q; }
+
+// sqrt and reciprocal by the hardware approximations (PTX sqrt.approx.f32,
+// rcp.approx.ftz.f32, relative error of a few ulp); used for the unit normal only.
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Eq. (14), delta = (eps/pi) / (eps^2 + u^2).
 __device__ __forceinline__ float dirac(float u, float eps) {
     return (eps * INV_PI) / (eps * eps + u * u);

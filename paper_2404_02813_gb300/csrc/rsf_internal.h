@@ -20,6 +20,10 @@ enum KernelId {
     KID_BX,        // group B, x pass
     KID_BY,        // group B, y pass
     KID_BZ,        // group B, z pass + data term, curvature and update epilogue
+    KID_TA_XY,     // tiled: group A, H products + x and y convolution
+    KID_TA_Z,      // tiled: group A, z convolution + local fits
+    KID_TB_XY,     // tiled: group B, x and y convolution
+    KID_TB_Z,      // tiled: group B, z convolution + data term, curvature, update
     KID_COUNT
 };
 const char *kernel_name(int id);
@@ -57,10 +61,16 @@ struct Fields {
     float *cs = nullptr;      // [0] m, [1] 1/s, [2] s^2, [3] s   (centring constants)
     float *partials = nullptr;// reduction scratch, 3 * kStatBlocks floats
     float *phi[2] = {nullptr, nullptr};
-    float *t[8] = {};         // stage buffers of the pass path
+    float *q[2] = {nullptr, nullptr};   // tiled path: +-atan(eps/|phi|)/pi of phi[i]
+    float *t[8] = {};         // stage buffers: one block of 8 * capacity floats, t[i] = t[0] + i * capacity,
+                              // capacity >= px * ny * nz (the tiled path's pitched fields use the block
+                              // as u (float4), ab and abxy (float2) at offsets 0, 4 np, 6 np)
+    int px = 0;               // x pitch of the tiled path's intermediate fields (multiple of 32)
+    int *err = nullptr;       // device error word written by bounded waits (0 = none)
 };
 
 constexpr int kStatBlocks = 1024;
+constexpr int kErrTimeout = 1;  // value of Fields::err after an expired bounded wait
 
 // Set-up: centring constants, centred image and the K*1 profiles.
 // `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
@@ -72,6 +82,16 @@ cudaError_t centre_image(const void *vol, int vt, Fields &f, cudaStream_t s);
 
 // Sets the calling thread's rsf_last_error() text.
 void set_last_error(const char *msg);
+
+// Tiled four-kernel path (rsf_tiled.cu) for the radii it is instantiated for.
+bool tiled_supports(int R);
+int tiled_pitch(int nx);
+cudaError_t tiled_prepare(int R);
+// q = +-atan(eps/|phi|)/pi (sign of phi) for the first tiled iteration.
+cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s);
+// One tiled iteration: reads phi_in and its q_in, writes phi_out and q_out.
+cudaError_t iterate_tiled(const Taps &taps, const Coeffs &c, Fields &f, const float *phi_in, const float *q_in,
+                          float *phi_out, float *q_out, float *stages, Profiler *prof, cudaStream_t s, int zc);
 
 // One iteration of the separable pass path: phi_in -> phi_out.
 // `stages`, when not null, receives RSF_NSTAGES fields (f1, f2, g, kappa, L).

@@ -25,7 +25,11 @@ RSF_U8, RSF_U16, RSF_F32 = 0, 1, 2
 STAGES = ("f1", "f2", "g", "kappa", "lap")
 
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
-            "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc")
+            "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
+            "rsf_set_option")
+
+OPT_PATH, OPT_ZCHUNK = 1, 2
+PATHS = {"auto": 0, "passes": 1, "tiled": 2}
 
 NOALLOC_MAX_VOXELS = 1 << 18
 
@@ -68,6 +72,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_prof_get.restype = i32
     L.rsf_evolve_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, vp]
     L.rsf_evolve_noalloc.restype = i32
+    L.rsf_set_option.argtypes = [vp, i32, i64]
+    L.rsf_set_option.restype = i32
     L.rsf_last_error.argtypes = []
     L.rsf_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -200,6 +206,13 @@ class Context:
         _check(load_library().rsf_step_stages(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi),
                                               _ptr(phi_next), _ptr(stages), *p.tuple()))
         return phi_next, stages
+
+    def set_option(self, key: int, value: int):
+        _check(load_library().rsf_set_option(self._h, int(key), int(value)))
+
+    def set_path(self, name: str):
+        """'auto' (tiled where instantiated, else passes), 'passes' or 'tiled'."""
+        self.set_option(OPT_PATH, PATHS[name])
 
     # kernel timing ---------------------------------------------------------
     def prof_enable(self, on: bool = True):

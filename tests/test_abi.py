@@ -65,3 +65,7 @@ def test_prof_names(lib):
     names = [lib.rsf_prof_name(k).decode() for k in range(n)]
     assert len(set(names)) == n and all(s.startswith("rsf_") for s in names)
     assert lib.rsf_prof_name(n) is None
+
+
+def test_set_option_rejects_bad_keys_without_a_context(lib):
+    assert lib.rsf_set_option(None, 1, 0) == -1

@@ -19,11 +19,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def ctx():
+@pytest.fixture(scope="module", params=["auto", "passes"])
+def ctx(request):
+    """Every test runs on the default (tiled) schedule and on the six-pass one."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     c = rsf.Context(0)
+    c.set_path(request.param)
     yield c
     c.close()
 

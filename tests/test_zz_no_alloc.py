@@ -25,6 +25,7 @@ def ctx():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     c = rsf.Context(0)
+    c.set_path("passes")   # the schedule rsf_evolve_noalloc runs
     yield c
     c.close()
 
