@@ -181,11 +181,12 @@ __global__ void __launch_bounds__(kXYThreads, ((NP == 2 && R <= 6) || (NP == 1 &
                 }
             }
             if (gx < d.nx) {
+                const int gy0 = y0 + warp * YT;
+                const long long q0 = (long long)z * oplane + (long long)gy0 * opx + gx;
 #pragma unroll
                 for (int o = 0; o < YT; ++o) {
-                    const int gy = y0 + warp * YT + o;
-                    if (gy < d.ny) {
-                        const long long q = (long long)z * oplane + (long long)gy * opx + gx;
+                    if (gy0 + o < d.ny) {
+                        const long long q = q0 + (long long)o * opx;
                         if (NP == 2) {
                             reinterpret_cast<float4 *>(out)[q] =
                                 make_float4(res[0][o].x, res[0][o].y, res[NP - 1][o].x, res[NP - 1][o].y);
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kAZThreads)
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < T; ++k) acc = f2fma(make_float2(t.g[k], t.g[k]), w[o + k], acc);
-            f1[o] = acc.x / acc.y;
+            f1[o] = __fdividef(acc.x, acc.y);
         }
     }
     float2 w[WIN];
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(kAZThreads)
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < T; ++k) acc = f2fma(make_float2(t.g[k], t.g[k]), w[o + k], acc);
-            const float f2 = acc.x / acc.y;
+            const float f2 = __fdividef(acc.x, acc.y);
             ab[(long long)zo * pplane + (long long)y * px + x] =
                 make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2));
             if (dump_f1) {
@@ -401,6 +402,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_bz(BZArgs A, Dims
     const float pxy = active ? __ldg(A.prof + x) * __ldg(A.prof + d.nx + y) : 0.f;
     const float *profz = A.prof + d.nx + d.ny;
     const float l12 = c.lambda1 - c.lambda2, s2 = A.cs[2];
+    const float eps_pi = c.eps * INV_PI, eps2 = c.eps * c.eps;
     const float *Iz = A.I + (long long)z0 * d.plane + col;
     float *Oz = A.phi_out + (long long)z0 * d.plane + col;
     float *Qz = A.q_out + (long long)z0 * d.plane + col;
@@ -445,7 +447,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_bz(BZArgs A, Dims
                         const float *n0 = snrm[zo & 3][0], *n1 = snrm[zo & 3][1];
                         const float kap = (n0[nc0 + 1] - n0[nc0 - 1]) * 0.5f + (n1[nc0 + NW] - n1[nc0 - NW]) * 0.5f +
                                           (snrm[(zo + 1) & 3][2][nc0] - snrm[(zo - 1) & 3][2][nc0]) * 0.5f;
-                        const float del = dirac(ph, c.eps);
+                        const float del = eps_pi * rcp_approx(eps2 + ph * ph);  // Eq. (14)
                         const float pn = ph + c.dt * (c.mu * (lap - kap) + del * (c.nu * kap - g));
                         *Oz = pn;
                         *Qz = heaviside_q_fast(pn, c.eps);
