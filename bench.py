@@ -32,21 +32,22 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # Algorithmic HBM bytes per voxel and launch of each per-iteration kernel: the
-# fields it must read once and write once (FP32), independent of tiling.
-ALGO_BYTES_PER_VOXEL = {
-    # six-pass schedule
-    "rsf_a_x": 4 + 4 + 16,   # phi, I -> four H-product fields
-    "rsf_a_y": 16 + 16,
-    "rsf_a_z": 16 + 8,       # four fields -> a, b
-    "rsf_b_x": 8 + 8,
-    "rsf_b_y": 8 + 8,
-    "rsf_b_z": 8 + 4 + 4 + 4,  # a, b, I, phi -> phi'
-    # tiled schedule
-    "rsf_ta_xy": 4 + 4 + 16,   # phi, I -> float4 of x/y-convolved H products
-    "rsf_ta_z": 16 + 8,        # float4 -> (a, b)
-    "rsf_tb_xy": 8 + 8,        # (a, b) -> x/y-convolved (a, b)
-    "rsf_tb_z": 8 + 4 + 4 + 4 + 4,  # (a, b), I, phi -> phi', q(phi')
-}
+# fields it must read once and write once, independent of tiling.  `img` is the
+# image's byte size (the tiled kernels read it in its own type), `st` the
+# storage byte size of the group-A fields and (a, b) (4, or 2 for FP16/BF16).
+def algo_bytes_per_voxel(img: int, st: int) -> dict:
+    return {
+        # six-pass schedule (FP32 fields, centred FP32 image)
+        "rsf_a_x": 4 + 4 + 16, "rsf_a_y": 16 + 16, "rsf_a_z": 16 + 8,
+        "rsf_b_x": 8 + 8, "rsf_b_y": 8 + 8, "rsf_b_z": 8 + 4 + 4 + 4,
+        # tiled schedule
+        "rsf_ta_xy": 4 + img + 4 * st,          # q, I -> four group-A fields
+        "rsf_ta_z": 4 * st + 2 * st,            # four fields -> (a, b)
+        "rsf_tb_xy": 2 * st + 8,                # (a, b) -> x/y-convolved (a, b), FP32
+        "rsf_tb_z": 8 + img + 4 + 4 + 4,        # (a, b)_xy, I, phi -> phi', q(phi')
+    }
+
+
 SETUP_LAUNCHES = 3  # statistics, their reduction, centring
 
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
@@ -210,6 +211,7 @@ def main():
     ap.add_argument("--size", type=int, default=None, help="cube edge instead of the workload's (profiling runs)")
     ap.add_argument("--iters", type=int, default=None, help="iterations per step instead of the workload's")
     ap.add_argument("--path", default="auto", choices=["auto", "passes", "tiled"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "rsf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -240,6 +242,7 @@ def main():
     out = torch.empty_like(ph0)
     ctx = rsf.Context(local)
     ctx.set_path(args.path)
+    ctx.set_storage(args.storage)
     stream = torch.cuda.ExternalStream(ctx.stream_handle)
 
     for _ in range(args.warmup):
@@ -296,7 +299,7 @@ def main():
         dom = max(prof, key=lambda k: prof[k][1])
         n_l, tot_ms = prof[dom]
         avg_s = tot_ms / max(n_l, 1) / 1e3
-        algo = ALGO_BYTES_PER_VOXEL[dom] * n_vox
+        algo = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2)[dom] * n_vox
         achieved = algo / avg_s / 1e9
         tr = NCU_TRAFFIC.get(dom)
         traffic = (tr["bytes_per_voxel"] * n_vox
@@ -305,9 +308,10 @@ def main():
         line = {
             "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "f32" else f"f32 compute, {args.storage} storage",
             "data": "synthetic (seeded vessel-network volume, light-sheet-like)",
-            "config": dict(workload_desc(args.workload, vol, params, iters),
+            "config": dict(workload_desc(args.workload, vol, params, iters), storage=args.storage,
                            parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",

@@ -125,13 +125,22 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   else the six-pass iteration; RSF_PATH_PASSES: always the
  *                   six-pass iteration; RSF_PATH_TILED: the tiled iteration
  *                   (other radii then fail with RSF_E_INVAL).
- *   RSF_OPT_ZCHUNK  z planes per CTA of the z-marching kernels; 0 (default)
+ *   RSF_OPT_ZCHUNK  z planes per CTA of the z-marching kernel; 0 (default)
  *                   picks enough chunks for about 16 CTAs per SM; else >= 8.
- * Both give the same arithmetic per voxel up to the order of FP32 rounding.
+ *                   Results do not depend on it.
+ *   RSF_OPT_STORAGE rsf_storage of the tiled path's intermediate fields: the
+ *                   four group-A fields (K*(H I), K*H, K*((1-H) I), K*(1-H)
+ *                   after the x and y passes) and the fits' combinations
+ *                   a, b; RSF_STORE_F32 (default), RSF_STORE_BF16 or
+ *                   RSF_STORE_F16.  Accumulation is FP32 throughout; phi, the
+ *                   image (read in its own type) and the x/y-convolved a, b
+ *                   stay exact / FP32.  16-bit storage needs the tiled path.
+ * The paths give the same result per voxel up to the order of FP32 rounding.
  * Errors: RSF_E_INVAL (unknown key or value).
  */
 #define RSF_OPT_PATH 1
 #define RSF_OPT_ZCHUNK 2
+#define RSF_OPT_STORAGE 3
 #define RSF_PATH_AUTO 0
 #define RSF_PATH_PASSES 1
 #define RSF_PATH_TILED 2

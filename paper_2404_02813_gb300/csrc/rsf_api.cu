@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "rsf.h"
 #include "rsf_internal.h"
@@ -112,7 +113,13 @@ struct rsf_ctx {
     rsf::Profiler prof;
     int opt_path = RSF_PATH_AUTO;
     int opt_zchunk = 0;
+    int opt_storage = RSF_STORE_F32;
+    rsf::BrickDev *d_bricks = nullptr;  // brick descriptors of the current launch group
+    int *d_starts = nullptr;            // 4 x (cap_bricks + 1) CTA offsets
+    int cap_bricks = 0;
 };
+
+
 
 static rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
     if (c->used + bytes > c->budget)
@@ -134,6 +141,52 @@ static void dev_free(rsf_ctx *c, void *p, size_t bytes) {
     c->used -= std::min<uint64_t>(c->used, bytes);
 }
 
+
+// Copy `nb` brick descriptors and their per-kernel CTA offsets to the device
+// and describe them as one launch group.
+static rsf_status upload_group(rsf_ctx *c, const rsf::BrickDev *b, int nb, int storage, int imgtype,
+                               const rsf::Taps &taps, rsf::TiledGroup *g) {
+    if (nb > c->cap_bricks) {
+        dev_free(c, c->d_bricks, sizeof(rsf::BrickDev) * (size_t)c->cap_bricks);
+        dev_free(c, c->d_starts, sizeof(int) * 4 * (size_t)(c->cap_bricks + 1));
+        c->d_bricks = nullptr;
+        c->d_starts = nullptr;
+        c->cap_bricks = 0;
+        const int cap = std::max(nb, 16);
+        rsf_status st = dev_alloc(c, (void **)&c->d_bricks, sizeof(rsf::BrickDev) * (size_t)cap);
+        if (st) return st;
+        st = dev_alloc(c, (void **)&c->d_starts, sizeof(int) * 4 * (size_t)(cap + 1));
+        if (st) return st;
+        c->cap_bricks = cap;
+    }
+    std::vector<int> starts(4 * (size_t)(nb + 1));
+    unsigned long long tot[4] = {0, 0, 0, 0};
+    for (int i = 0; i < nb; ++i) {
+        unsigned cnt[4];
+        rsf::tiled_cta_counts(b[i], cnt);
+        for (int k = 0; k < 4; ++k) {
+            starts[(size_t)k * (nb + 1) + i] = (int)tot[k];
+            tot[k] += cnt[k];
+        }
+    }
+    for (int k = 0; k < 4; ++k) {
+        if (tot[k] >= (1ull << 31)) return fail(RSF_E_INVAL, "launch group too large (%llu CTAs)", tot[k]);
+        starts[(size_t)k * (nb + 1) + nb] = (int)tot[k];
+    }
+    RSF_CUDA(cudaMemcpyAsync(c->d_bricks, b, sizeof(rsf::BrickDev) * nb, cudaMemcpyHostToDevice, c->stream));
+    RSF_CUDA(cudaMemcpyAsync(c->d_starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice,
+                             c->stream));
+    g->storage = storage;
+    g->imgtype = imgtype;
+    g->taps = taps;
+    g->bricks = c->d_bricks;
+    g->nb = nb;
+    for (int k = 0; k < 4; ++k) {
+        g->starts[k] = c->d_starts + (size_t)k * (nb + 1);
+        g->ncta[k] = (unsigned)tot[k];
+    }
+    return RSF_OK;
+}
 
 static void free_fields(rsf_ctx *c) {
     size_t fb = sizeof(float) * (size_t)c->cap_n;
@@ -298,6 +351,8 @@ extern "C" void rsf_destroy(rsf_ctx *c) {
         dev_free(c, c->f.err, sizeof(int));
         dev_free(c, c->staging, c->staging_cap);
         dev_free(c, c->dump, c->dump_cap);
+        dev_free(c, c->d_bricks, sizeof(rsf::BrickDev) * (size_t)c->cap_bricks);
+        dev_free(c, c->d_starts, sizeof(int) * 4 * (size_t)(c->cap_bricks + 1));
         c->prof.release();
         cudaStreamDestroy(c->stream);
     }
@@ -338,32 +393,62 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     if ((st = device_volume(c, volume, vt, n, &vol))) return st;
     const rsf::Taps taps = make_taps(sigma);
     const rsf::Coeffs co{eps, lambda1, lambda2, nu, mu, dt};
-    RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream));
-    RSF_CUDA(cudaMemcpyAsync(f.phi[0], phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    const int storage = c->opt_storage;
     const bool tiled = c->opt_path != RSF_PATH_PASSES && rsf::tiled_supports(taps.R);
     if (c->opt_path == RSF_PATH_TILED && !tiled)
         return fail(RSF_E_INVAL, "the tiled path has no kernels for radius %d", taps.R);
-    int zc = c->opt_zchunk;
+    if (storage != RSF_STORE_F32 && !tiled)
+        return fail(RSF_E_INVAL, "16-bit storage needs the tiled path (radius %d, path option %d)", taps.R, c->opt_path);
+    // the tiled path reads the image in its own type and centres it on load
+    RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream, !tiled));
+    RSF_CUDA(cudaMemcpyAsync(f.phi[0], phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
+    int cur = 0;
     if (tiled) {
-        RSF_CUDA(rsf::tiled_prepare(taps.R));
-        if (zc <= 0) {  // enough z chunks for about 16 CTAs per SM
+        RSF_CUDA(rsf::tiled_prepare(storage, taps.R));
+        rsf::BrickDev b{};
+        b.nx = (int)nx;
+        b.ny = (int)ny;
+        b.nz = (int)nz;
+        b.px = f.px;
+        b.img = vol;
+        b.cs = f.cs;
+        b.prof = f.prof;
+        b.phi[0] = f.phi[0];
+        b.phi[1] = f.phi[1];
+        b.q[0] = f.q[0];
+        b.q[1] = f.q[1];
+        rsf::tiled_stage_views(storage, f.t[0], (long long)f.px * ny * nz, &b.u4, &b.ab, &b.abxy);
+        b.eps = eps;
+        b.lambda1 = lambda1;
+        b.lambda2 = lambda2;
+        b.nu = nu;
+        b.mu = mu;
+        b.dt = dt;
+        b.zc = c->opt_zchunk;
+        if (b.zc <= 0) {  // enough z chunks for about 16 CTAs per SM
             int sms = 0;
             RSF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
             const long long nxy = (long long)((nx + 31) / 32) * ((ny + 7) / 8);
             const long long chunks = std::max<long long>(1, (16LL * sms + nxy - 1) / nxy);
-            zc = (int)std::max<long long>(16, (nz + chunks - 1) / chunks);
+            b.zc = (int)std::max<long long>(16, (nz + chunks - 1) / chunks);
         }
-    }
-    RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
-    if (tiled && iters > 0) RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
-    int cur = 0;
-    for (int it = 0; it < iters; ++it) {
-        float *d_it = it == iters - 1 ? dump : nullptr;
-        cudaError_t e = tiled ? rsf::iterate_tiled(taps, co, f, f.phi[cur], f.q[cur], f.phi[cur ^ 1], f.q[cur ^ 1], d_it,
-                                                   &c->prof, c->stream, zc)
-                              : rsf::iterate_passes(taps, co, f, f.phi[cur], f.phi[cur ^ 1], d_it, &c->prof, c->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
-        cur ^= 1;
+        b.dump = dump;  // only rsf_step_stages asks for stages, and it runs one iteration
+        rsf::TiledGroup g{};
+        if ((st = upload_group(c, &b, 1, storage, (int)vt, taps, &g))) return st;
+        if (iters > 0) RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
+        for (int it = 0; it < iters; ++it) {
+            cudaError_t e = rsf::tiled_iterate(g, it & 1, &c->prof, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+        }
+        cur = iters & 1;
+    } else {
+        for (int it = 0; it < iters; ++it) {
+            float *d_it = it == iters - 1 ? dump : nullptr;
+            cudaError_t e = rsf::iterate_passes(taps, co, f, f.phi[cur], f.phi[cur ^ 1], d_it, &c->prof, c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "iteration launch");
+            cur ^= 1;
+        }
     }
     RSF_CUDA(cudaMemcpyAsync(phi_out, f.phi[cur], sizeof(float) * n, cudaMemcpyDefault, c->stream));
     if (stages && dump != stages)
@@ -407,6 +492,11 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
         case RSF_OPT_PATH:
             if (value < RSF_PATH_AUTO || value > RSF_PATH_TILED) return fail(RSF_E_INVAL, "unknown path %lld", (long long)value);
             c->opt_path = (int)value;
+            return RSF_OK;
+        case RSF_OPT_STORAGE:
+            if (value != RSF_STORE_F32 && value != RSF_STORE_BF16 && value != RSF_STORE_F16)
+                return fail(RSF_E_INVAL, "unknown storage %lld", (long long)value);
+            c->opt_storage = (int)value;
             return RSF_OK;
         case RSF_OPT_ZCHUNK:
             if (value < 0 || value > (1 << 20)) return fail(RSF_E_INVAL, "z chunk must lie in [0, 2^20]");

@@ -72,9 +72,9 @@ struct Fields {
 constexpr int kStatBlocks = 1024;
 constexpr int kErrTimeout = 1;  // value of Fields::err after an expired bounded wait
 
-// Set-up: centring constants, centred image and the K*1 profiles.
-// `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
-cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s);
+// Set-up: centring constants, the K*1 profiles and (when `centre`) the
+// centred image f.I.  `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
+cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s, bool centre = true);
 
 // The centring half of setup_image alone (statistics and centred image, no
 // profiles); enqueues on `s` and never synchronises.
@@ -83,15 +83,42 @@ cudaError_t centre_image(const void *vol, int vt, Fields &f, cudaStream_t s);
 // Sets the calling thread's rsf_last_error() text.
 void set_last_error(const char *msg);
 
-// Tiled four-kernel path (rsf_tiled.cu) for the radii it is instantiated for.
+// One brick of the tiled path: an independent volume with its own fields and
+// scalars.  Device copies of these descriptors drive the batched launches.
+struct BrickDev {
+    int nx, ny, nz, px;     // dimensions; x pitch of the intermediate fields
+    const void *img;        // image, nx*ny*nz values of the group's image type
+    const float *cs;        // centring constants [m, 1/s, s^2, s]
+    const float *prof;      // K*1 profiles p_x[nx], p_y[ny], p_z[nz]
+    float *phi[2], *q[2];   // ping-pong level set and its q = +-atan(eps/|phi|)/pi
+    void *u4, *ab;          // pitched group-A fields (4 per voxel) and (a, b), storage type
+    float2 *abxy;           // pitched x/y-convolved (a, b), FP32
+    float eps, lambda1, lambda2, nu, mu, dt;
+    int zc;                 // z chunk of the update kernel
+    float *dump;            // optional 5 * n stage fields (f1, f2, g, kappa, L)
+};
+
+// A set of bricks launched together: same radius, image type and storage.
+struct TiledGroup {
+    int storage;            // 0 FP32, 1 BF16, 2 FP16 (rsf_storage)
+    int imgtype;            // 0 uint8, 1 uint16, 2 float
+    Taps taps;
+    const BrickDev *bricks; // device array of nb descriptors
+    int nb;
+    const int *starts[4];   // device: per kernel, nb + 1 CTA offsets
+    unsigned ncta[4];       // CTAs per kernel launch
+};
+
+// Tiled four-kernel path (rsf_tiled*.cu) for the radii it is instantiated for.
 bool tiled_supports(int R);
 int tiled_pitch(int nx);
-cudaError_t tiled_prepare(int R);
-// q = +-atan(eps/|phi|)/pi (sign of phi) for the first tiled iteration.
+cudaError_t tiled_prepare(int storage, int R);
+cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
+void tiled_cta_counts(const BrickDev &b, unsigned counts[4]);
+size_t tiled_stage_bytes(int storage, long long np);
+void tiled_stage_views(int storage, void *base, long long np, void **u4, void **ab, float2 **abxy);
+// q = +-atan(eps/|phi|)/pi (sign of phi) before the first tiled iteration.
 cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s);
-// One tiled iteration: reads phi_in and its q_in, writes phi_out and q_out.
-cudaError_t iterate_tiled(const Taps &taps, const Coeffs &c, Fields &f, const float *phi_in, const float *q_in,
-                          float *phi_out, float *q_out, float *stages, Profiler *prof, cudaStream_t s, int zc);
 
 // One iteration of the separable pass path: phi_in -> phi_out.
 // `stages`, when not null, receives RSF_NSTAGES fields (f1, f2, g, kappa, L).

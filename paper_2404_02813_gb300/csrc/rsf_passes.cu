@@ -277,7 +277,7 @@ static void launch_s(Outs<NF> in, Epi epi, const Dims &d, const Taps &t, int axi
     k_spass<NF, Epi><<<grid, dim3(kSX, kSY), 0, s>>>(in, epi, d, t, axis);
 }
 
-cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s) {
+cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s, bool centre) {
     const Dims &d = f.d;
     const int eb = 1184;  // elementwise grid: a multiple of the SM count, grid-stride beyond
     switch (vt) {
@@ -291,10 +291,12 @@ cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cu
             k_stats<float><<<kStatBlocks, 256, 0, s>>>((const float *)vol, d.n, f.partials);
     }
     k_stats_final<<<1, kStatBlocks, 0, s>>>(f.partials, d.n, f.cs);
-    switch (vt) {
-        case 0: k_center<uint8_t><<<eb, 256, 0, s>>>((const uint8_t *)vol, d.n, f.cs, f.I); break;
-        case 1: k_center<uint16_t><<<eb, 256, 0, s>>>((const uint16_t *)vol, d.n, f.cs, f.I); break;
-        default: k_center<float><<<eb, 256, 0, s>>>((const float *)vol, d.n, f.cs, f.I);
+    if (centre) {
+        switch (vt) {
+            case 0: k_center<uint8_t><<<eb, 256, 0, s>>>((const uint8_t *)vol, d.n, f.cs, f.I); break;
+            case 1: k_center<uint16_t><<<eb, 256, 0, s>>>((const uint16_t *)vol, d.n, f.cs, f.I); break;
+            default: k_center<float><<<eb, 256, 0, s>>>((const float *)vol, d.n, f.cs, f.I);
+        }
     }
     // zero-padding profiles p_a(i) = sum_{k: 0 <= i+k < n_a} g[k]: K*1 = p_x p_y p_z
     std::vector<float> prof((size_t)d.nx + d.ny + d.nz);

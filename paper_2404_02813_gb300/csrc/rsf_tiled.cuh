@@ -1,0 +1,673 @@
+// rsf_tiled.cuh -- the tiled four-kernel RSF iteration (arXiv 2404.02813,
+// Sec. 3 and 4.2) over a table of bricks.
+//
+// A launch covers every brick of one group (same kernel radius R and image
+// type); a plain volume is a group of one brick.  Each brick is an independent
+// volume with its own boundaries, fields and scalars (the sub-volumes of the
+// paper's volume-level parallelism, Sec. 4.1).  A CTA finds its brick by a
+// binary search over the per-kernel CTA offsets of the group.
+//
+//   rsf_ta_xy  per z-plane, a 32x32 output tile plus an R halo in shared
+//              memory: forms H I~, H, (1-H) I~, 1-H (Eqs. 6, 8-10) from the
+//              image (centred on load) and q = +-atan(eps/|phi|)/pi, convolves
+//              them along x then y (field pairs share packed f32x2 FMAs) and
+//              stores them (FP32, FP16 or BF16 storage).
+//   rsf_ta_z   x-z slabs (32 columns x 64 output planes) loaded into shared
+//              memory all at once; z convolution over a register window; the
+//              local fits f1 = K*(H I)/K*H, f2 = K*((1-H) I)/K*(1-H), and
+//              a = l1 f1 - l2 f2, b = l1 f1^2 - l2 f2^2.
+//   rsf_tb_xy  the x/y kernel on (a, b); its output stays FP32 (the data term
+//              below is a difference of terms much larger than itself).
+//   rsf_tb_z   a z march over a 32x8 column tile: a register ring of (a, b)
+//              planes, a phi ring and a unit-normal ring in shared memory
+//              (each normal computed once per voxel);
+//              g = s^2 [ (l1 - l2) K1 I~^2 - 2 I~ K*a + K*b ]  (Eqs. 11-12),
+//              kappa and the Laplacian (Eqs. 3-4), the update of Eqs. (1),
+//              (13), (14), and q of the new phi for the next rsf_ta_xy.
+//
+// Convolutions use zero padding, taps summed k = -R..R, FP32 accumulation;
+// finite differences use reflect-101 for phi and for the normal.  The
+// intermediate fields are stored with an x pitch rounded up to 32 columns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rsf_internal.h"
+
+namespace rsf {
+namespace tiled {
+
+constexpr int kXYT = 32;          // x/y kernel: output tile edge (x and y)
+constexpr int kXYThreads = 256;   // 8 warps
+constexpr int kXYPlanes = 8;      // z-planes per CTA of the x/y kernel
+constexpr int kZX = 32, kZY = 8;  // z march: columns per CTA
+constexpr int kZThreads = kZX * kZY;
+constexpr int kAZT = 64;          // x-z slab: output planes per CTA
+constexpr int kAZThreads = 256;
+constexpr int kAZO = kAZT / (kAZThreads / 32);
+constexpr int kPFB = 2;           // (a, b) planes loaded ahead in the z march
+
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// ------------------------------------------------------------- storage
+
+template <class S> struct Store;
+template <> struct Store<float> {
+    using V4 = float4;
+    using V2 = float2;
+    __device__ __forceinline__ static V4 pack4(float4 v) { return v; }
+    __device__ __forceinline__ static float4 unpack4(V4 v) { return v; }
+    __device__ __forceinline__ static V2 pack2(float2 v) { return v; }
+    __device__ __forceinline__ static float2 unpack2(V2 v) { return v; }
+};
+template <> struct Store<__half> {
+    using V4 = uint2;
+    using V2 = uint32_t;
+    __device__ __forceinline__ static uint32_t p(float a, float b) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __device__ __forceinline__ static float2 u(uint32_t w) { return __half22float2(*reinterpret_cast<__half2 *>(&w)); }
+    __device__ __forceinline__ static V4 pack4(float4 v) { return make_uint2(p(v.x, v.y), p(v.z, v.w)); }
+    __device__ __forceinline__ static float4 unpack4(V4 v) {
+        const float2 a = u(v.x), b = u(v.y);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static V2 pack2(float2 v) { return p(v.x, v.y); }
+    __device__ __forceinline__ static float2 unpack2(V2 v) { return u(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    using V4 = uint2;
+    using V2 = uint32_t;
+    __device__ __forceinline__ static uint32_t p(float a, float b) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __device__ __forceinline__ static float2 u(uint32_t w) {
+        return __bfloat1622float2(*reinterpret_cast<__nv_bfloat162 *>(&w));
+    }
+    __device__ __forceinline__ static V4 pack4(float4 v) { return make_uint2(p(v.x, v.y), p(v.z, v.w)); }
+    __device__ __forceinline__ static float4 unpack4(V4 v) {
+        const float2 a = u(v.x), b = u(v.y);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    __device__ __forceinline__ static V2 pack2(float2 v) { return p(v.x, v.y); }
+    __device__ __forceinline__ static float2 unpack2(V2 v) { return u(v); }
+};
+
+// Image value, centred and scaled on load: (I - m) / s = I * (1/s) + (-m/s),
+// one rounding (1/s is a power of two), the same value the centring kernel stores.
+template <class T>
+__device__ __forceinline__ float centred(const T *img, long long p, float inv_s, float nms) {
+    return fmaf((float)__ldg(img + p), inv_s, nms);
+}
+
+// ------------------------------------------------------------ brick table
+
+__device__ __forceinline__ int find_brick(const int *__restrict__ starts, int nb, int cta) {
+    int lo = 0, hi = nb;  // starts[lo] <= cta < starts[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(starts + mid) <= cta) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct GroupArgs {
+    const BrickDev *bricks;
+    const int *starts;  // nb + 1 CTA offsets of this kernel within the launch
+    int nb;
+    int parity;         // iteration parity: reads phi[parity], q[parity], writes the other
+};
+
+// ---------------------------------------------------------------- x / y
+
+template <class ImgT>
+struct ProHP {  // (H I~, H), ((1-H) I~, 1-H) from q and the centred image
+    const float *q;
+    const ImgT *img;
+    float inv_s, nms;
+    struct Raw { float q, im; };
+    __device__ __forceinline__ Raw fetch(long long p) const { return Raw{__ldg(q + p), centred(img, p, inv_s, nms)}; }
+    __device__ __forceinline__ Raw zero() const { return Raw{0.f, 0.f}; }
+    __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
+        if (inside) {
+            const float h = h_of_q(r.q), hc = hc_of_q(r.q);
+            v[0] = make_float2(h * r.im, h);
+            v[1] = make_float2(hc * r.im, hc);
+        } else {
+            v[0] = v[1] = make_float2(0.f, 0.f);
+        }
+    }
+};
+
+template <class S>
+struct ProAB {  // (a, b) as stored by rsf_ta_z (pitched)
+    const typename Store<S>::V2 *ab;
+    using Raw = typename Store<S>::V2;
+    __device__ __forceinline__ Raw fetch(long long p) const { return __ldg(ab + p); }
+    __device__ __forceinline__ Raw zero() const { return Raw{}; }
+    __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
+        v[0] = inside ? Store<S>::unpack2(r) : make_float2(0.f, 0.f);
+    }
+};
+
+// Shared-memory layout of the x/y kernel (float2 units).
+template <int R, int NP>
+struct XYLayout {
+    static constexpr int W = kXYT + 2 * R;              // loaded width
+    static constexpr int H = kXYT + 2 * R;              // loaded rows
+    static constexpr int P = ((W + 15) / 16) * 16 + 1;  // row pitch = 1 (mod 16): conflict-free float2 reads
+    static constexpr int IN = NP * H * P;               // input tile
+    static constexpr int XC = NP * H * kXYT;            // x-convolved rows
+    static constexpr size_t bytes = sizeof(float2) * (IN + XC);
+};
+
+template <int R, int NP>
+constexpr int xy_min_blocks() { return R <= 6 ? 3 : 2; }
+
+// The x/y kernel body for one CTA of one brick: planes [za, za + kXYPlanes) of
+// tile (x0, y0).  The global loads of plane z+1 are issued right after the
+// first barrier of plane z and land in registers while the convolutions run.
+// Input row pitch `ipx`; output pitch `opx`; `Out` writes the NP pairs.
+template <int R, int NP, class Pro, class Out>
+__device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, int ny, int nz, int ipx, int x0,
+                                        int y0, int za, const Taps &t, float2 *sm) {
+    using L = XYLayout<R, NP>;
+    using Raw = typename Pro::Raw;
+    constexpr int T = 2 * R + 1;
+    constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
+    constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
+    constexpr int NE = (L::H * L::W + kXYThreads - 1) / kXYThreads;  // tile entries per thread
+    static_assert(NE <= 32, "tile entries per thread exceed the mask");
+    float2 *in = sm;
+    float2 *xc = sm + L::IN;
+    float2 gg[T];
+#pragma unroll
+    for (int k = 0; k < T; ++k) gg[k] = make_float2(t.g[k], t.g[k]);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int zb_end = min(za + kXYPlanes, nz);
+    const long long iplane = (long long)ipx * ny;
+
+    int eoff[NE], esm[NE];
+    unsigned inside = 0;
+#pragma unroll
+    for (int e = 0; e < NE; ++e) {
+        const int i = threadIdx.x + e * kXYThreads;
+        const int ii = min(i, L::H * L::W - 1);
+        const int ly = ii / L::W, lx = ii - ly * L::W;
+        const int gx = x0 + lx - R, gy = y0 + ly - R;
+        const bool in_vol = i < L::H * L::W && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        eoff[e] = in_vol ? gy * ipx + gx : 0;
+        esm[e] = i < L::H * L::W ? ly * L::P + lx : -1;
+        inside |= (in_vol ? 1u : 0u) << e;
+    }
+    Raw raw[NE];
+    auto fetch = [&](int z) {
+        const long long zb = (long long)z * iplane;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) raw[e] = ((inside >> e) & 1u) ? pro.fetch(zb + eoff[e]) : pro.zero();
+    };
+    fetch(za);
+    for (int z = za; z < zb_end; ++z) {
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            if (esm[e] >= 0) {
+                float2 v[NP];
+                pro.apply(raw[e], (inside >> e) & 1u, v);
+#pragma unroll
+                for (int p = 0; p < NP; ++p) in[p * L::H * L::P + esm[e]] = v[p];
+            }
+        }
+        __syncthreads();
+        if (z + 1 < zb_end) fetch(z + 1);
+        {
+            const int h = lane >> 4, r = (lane >> 2) & 3, g = lane & 3;
+            for (int item = warp; item < NP * NRB * 2; item += kXYThreads / 32) {
+                const int p = item / (NRB * 2);
+                const int rem = item - p * NRB * 2;
+                const int row = (rem >> 1) * 8 + h * 4 + r;
+                const int xo = (rem & 1) * 16 + g * XT;
+                if (row < L::H) {
+                    const float2 *src = in + (p * L::H + row) * L::P + xo;
+                    float2 w[XT + 2 * R];
+#pragma unroll
+                    for (int j = 0; j < XT + 2 * R; ++j) w[j] = src[j];
+#pragma unroll
+                    for (int o = 0; o < XT; ++o) {
+                        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k < T; ++k) acc = f2fma(gg[k], w[o + k], acc);
+                        xc[(p * L::H + row) * kXYT + xo + o] = acc;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        {
+            const int gx = x0 + lane;
+            float2 res[NP][YT];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                float2 w[YT + 2 * R];
+#pragma unroll
+                for (int j = 0; j < YT + 2 * R; ++j) w[j] = xc[(p * L::H + warp * YT + j) * kXYT + lane];
+#pragma unroll
+                for (int o = 0; o < YT; ++o) {
+                    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < T; ++k) acc = f2fma(gg[k], w[o + k], acc);
+                    res[p][o] = acc;
+                }
+            }
+            if (gx < nx) {
+                const int gy0 = y0 + warp * YT;
+#pragma unroll
+                for (int o = 0; o < YT; ++o)
+                    if (gy0 + o < ny) out(z, gy0 + o, gx, res[0][o], res[NP - 1][o]);
+            }
+        }
+        __syncthreads();  // the next plane reuses the tiles
+    }
+}
+
+template <class S>
+struct OutU4 {  // four H-product fields -> pitched storage
+    typename Store<S>::V4 *u;
+    int px;
+    long long pplane;
+    __device__ __forceinline__ void operator()(int z, int y, int x, float2 a, float2 b) const {
+        u[(long long)z * pplane + (long long)y * px + x] = Store<S>::pack4(make_float4(a.x, a.y, b.x, b.y));
+    }
+};
+struct OutAB {  // x/y-convolved (a, b), FP32, pitched
+    float2 *ab;
+    int px;
+    long long pplane;
+    __device__ __forceinline__ void operator()(int z, int y, int x, float2 a, float2) const {
+        ab[(long long)z * pplane + (long long)y * px + x] = a;
+    }
+};
+
+// CTA -> (brick, tile) for the x/y kernels: tiles (tx, ty, tz) of 32 x 32 x kXYPlanes.
+struct XYTile {
+    int b, x0, y0, za;
+};
+__device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev &B, int b) {
+    const int local = blockIdx.x - __ldg(G.starts + b);
+    const int ntx = (B.nx + kXYT - 1) / kXYT, nty = (B.ny + kXYT - 1) / kXYT;
+    const int tx = local % ntx, r = local / ntx;
+    return XYTile{b, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes};
+}
+
+template <int R, class ImgT, class S>
+__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 2>()) k_ta_xy(GroupArgs G, Taps t) {
+    extern __shared__ float2 sm[];
+    const int b = find_brick(G.starts, G.nb, blockIdx.x);
+    const BrickDev &B = G.bricks[b];
+    const XYTile tl = xy_tile_of(G, B, b);
+    const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
+    ProHP<ImgT> pro{G.parity ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
+    OutU4<S> out{reinterpret_cast<typename Store<S>::V4 *>(B.u4), B.px, (long long)B.px * B.ny};
+    xy_tile<R, 2>(pro, out, B.nx, B.ny, B.nz, B.nx, tl.x0, tl.y0, tl.za, t, sm);
+}
+
+template <int R, class S>
+__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 1>()) k_tb_xy(GroupArgs G, Taps t) {
+    extern __shared__ float2 sm[];
+    const int b = find_brick(G.starts, G.nb, blockIdx.x);
+    const BrickDev &B = G.bricks[b];
+    const XYTile tl = xy_tile_of(G, B, b);
+    ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
+    OutAB out{B.abxy, B.px, (long long)B.px * B.ny};
+    xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.px, tl.x0, tl.y0, tl.za, t, sm);
+}
+
+// ------------------------------------------------------------------ A: z
+
+// x-z slab: 32 columns of one y row, kAZT output planes; every load of the
+// slab in flight at once, then a register-window convolution per lane.  The
+// slab is held as two float2 arrays so that window reads are conflict-free.
+// Consecutive CTAs take consecutive z slabs of one row (shared halos hit L2).
+template <int R>
+constexpr size_t az_smem() { return sizeof(float2) * 2 * (kAZT + 2 * R) * 32; }
+
+template <int R, class S>
+__global__ void __launch_bounds__(kAZThreads, R <= 6 ? 4 : (R <= 8 ? 3 : 2)) k_ta_z(GroupArgs G, Taps t) {
+    constexpr int T = 2 * R + 1;
+    constexpr int ROWS = kAZT + 2 * R;
+    constexpr int WIN = kAZO + 2 * R;
+    using V4 = typename Store<S>::V4;
+    using V2 = typename Store<S>::V2;
+    extern __shared__ float2 slab[];  // [2][ROWS][32]
+    const int b = find_brick(G.starts, G.nb, blockIdx.x);
+    const BrickDev &B = G.bricks[b];
+    const int local = blockIdx.x - __ldg(G.starts + b);
+    const int nzt = (B.nz + kAZT - 1) / kAZT, nxt = (B.nx + 31) / 32;
+    const int zt = local % nzt;
+    const int rest = local / nzt;
+    const int xt = rest % nxt, y = rest / nxt;
+    const int x0 = xt * 32, z0 = zt * kAZT;
+    const int px = B.px;
+    const long long pplane = (long long)px * B.ny;
+    const V4 *src = reinterpret_cast<const V4 *>(B.u4) + (long long)y * px + x0;
+
+    for (int i = threadIdx.x; i < ROWS * 32; i += kAZThreads) {
+        const int row = i >> 5, col = i & 31;
+        const int zi = z0 - R + row;
+        const float4 v = ((unsigned)zi < (unsigned)B.nz) ? Store<S>::unpack4(__ldg(src + (long long)zi * pplane + col))
+                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        slab[row * 32 + col] = make_float2(v.x, v.y);
+        slab[(ROWS + row) * 32 + col] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = x0 + lane;
+    const int zb = warp * kAZO;
+    if (x >= B.nx) return;
+    const float l1 = B.lambda1, l2 = B.lambda2;
+    float f1[kAZO];
+    {
+        float2 w[WIN];
+#pragma unroll
+        for (int j = 0; j < WIN; ++j) w[j] = slab[(zb + j) * 32 + lane];
+#pragma unroll
+        for (int o = 0; o < kAZO; ++o) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < T; ++k) acc = f2fma(make_float2(t.g[k], t.g[k]), w[o + k], acc);
+            f1[o] = __fdividef(acc.x, acc.y);
+        }
+    }
+    float2 w[WIN];
+#pragma unroll
+    for (int j = 0; j < WIN; ++j) w[j] = slab[(ROWS + zb + j) * 32 + lane];
+    V2 *ab = reinterpret_cast<V2 *>(B.ab);
+#pragma unroll
+    for (int o = 0; o < kAZO; ++o) {
+        const int zo = z0 + zb + o;
+        if (zo < B.nz) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < T; ++k) acc = f2fma(make_float2(t.g[k], t.g[k]), w[o + k], acc);
+            const float f2 = __fdividef(acc.x, acc.y);
+            ab[(long long)zo * pplane + (long long)y * px + x] =
+                Store<S>::pack2(make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2)));
+            if (B.dump) {
+                const long long q = (long long)zo * B.nx * B.ny + (long long)y * B.nx + x;
+                const long long n = (long long)B.nx * B.ny * B.nz;
+                B.dump[q] = f1[o] * B.cs[3] + B.cs[0];
+                B.dump[n + q] = f2 * B.cs[3] + B.cs[0];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ B: z
+
+// q = +-atan(eps/|u|)/pi (the small side of H, sign of u), with the atan
+// argument kept in [0, 1]: for |u| < eps, atan(eps/|u|) = pi/2 - atan(|u|/eps).
+__device__ __forceinline__ float heaviside_q_fast(float u, float eps) {
+    const float a = fabsf(u);
+    const float r = a >= eps ? atanf(__fdividef(eps, a)) * INV_PI : 0.5f - atanf(__fdividef(a, eps)) * INV_PI;
+    return copysignf(r, u);
+}
+
+// z march over a 32x8 column tile of one brick, z chunk [z0, z0 + zc).
+// Output step zo:  store phi plane zo+3 (loaded into registers one step earlier)
+//                  and issue the loads of plane zo+4;  barrier;
+//                  normals of plane zo+2;  output of plane zo, which reads the
+//                  normals of zo-1, zo, zo+1 written in earlier steps.
+// Rings (logical plane p in slot p & (size-1)): phi 8 planes (zo-2 .. zo+3 live),
+// normals 4 planes (zo-1 .. zo+2 live).  The reflected tile offsets do not
+// depend on z and are computed once.  The (a, b) window is a register ring of
+// 2R+1+kPFB slots (plane s in slot s mod (2R+1+kPFB)); the load of plane
+// s+kPFB goes straight into its slot, so the body unrolled over the ring has
+// static indices.
+template <int R, class ImgT>
+__global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_tb_z(GroupArgs G, Taps t) {
+    constexpr int T = 2 * R + 1;
+    constexpr int M = T + kPFB;
+    constexpr int PW = kZX + 4, PH = kZY + 4;  // phi tile: halo 2
+    constexpr int NW = kZX + 2, NH = kZY + 2;  // normal tile: halo 1
+    constexpr int NPE = (PH * PW + kZThreads - 1) / kZThreads;
+    constexpr int NNE = (NH * NW + kZThreads - 1) / kZThreads;
+    __shared__ float sphi[8][PH * PW];
+    __shared__ float snrm[4][3][NH * NW];
+
+    const int bi = find_brick(G.starts, G.nb, blockIdx.x);
+    const BrickDev &B = G.bricks[bi];
+    const int local = blockIdx.x - __ldg(G.starts + bi);
+    const int nbx = (B.nx + kZX - 1) / kZX, nby = (B.ny + kZY - 1) / kZY;
+    const int bx = local % nbx, rr = local / nbx;
+    const int nx = B.nx, ny = B.ny, nz = B.nz;
+    const long long plane = (long long)nx * ny;
+    const int zc = B.zc;
+
+    const int tx = threadIdx.x & (kZX - 1), ty = threadIdx.x / kZX;
+    const int x0 = bx * kZX, y0 = (rr % nby) * kZY;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < nx && y < ny;
+    const int z0 = (rr / nby) * zc;
+    const int z1 = min(z0 + zc, nz);
+    const int nsteps = (z1 - z0) + 2 * R;
+    const long long col = (long long)min(y, ny - 1) * nx + min(x, nx - 1);
+    const int px = B.px;
+    const long long pplane = (long long)px * ny;
+    const float *phi = G.parity ? B.phi[1] : B.phi[0];
+
+    int poff[NPE], noff[NNE];
+#pragma unroll
+    for (int e = 0; e < NPE; ++e) {
+        const int i = min((int)threadIdx.x + e * kZThreads, PH * PW - 1);
+        const int ly = i / PW, lx = i - ly * PW;
+        const int gx = refl101(clampi(x0 + lx - 2, -2, nx + 1), nx);
+        const int gy = refl101(clampi(y0 + ly - 2, -2, ny + 1), ny);
+        poff[e] = gy * nx + gx;
+    }
+#pragma unroll
+    for (int e = 0; e < NNE; ++e) {
+        const int i = min((int)threadIdx.x + e * kZThreads, NH * NW - 1);
+        const int ly = i / NW, lx = i - ly * NW;
+        const int qx = refl101(clampi(x0 + lx - 1, -1, nx), nx);
+        const int qy = refl101(clampi(y0 + ly - 1, -1, ny), ny);
+        noff[e] = clampi(qy - y0 + 2, 1, PH - 2) * PW + clampi(qx - x0 + 2, 1, PW - 2);
+    }
+    auto fetch_phi = [&](int lz, float *v) {
+        const float *src = phi + (long long)refl101(clampi(lz, -2, nz + 1), nz) * plane;
+#pragma unroll
+        for (int e = 0; e < NPE; ++e) v[e] = __ldg(src + poff[e]);
+    };
+    auto store_phi = [&](int lz, const float *v) {
+        float *dst = sphi[lz & 7];
+#pragma unroll
+        for (int e = 0; e < NPE; ++e)
+            if ((int)threadIdx.x + e * kZThreads < PH * PW) dst[threadIdx.x + e * kZThreads] = v[e];
+    };
+    auto normals = [&](int lz) {
+        const int q = refl101(clampi(lz, -1, nz), nz);  // physical plane; q-1..q+1 are in the phi ring
+        const float *pm = sphi[(q - 1) & 7], *pc = sphi[q & 7], *pp = sphi[(q + 1) & 7];
+        float *n0 = snrm[lz & 3][0], *n1 = snrm[lz & 3][1], *n2 = snrm[lz & 3][2];
+#pragma unroll
+        for (int e = 0; e < NNE; ++e) {
+            const int i = threadIdx.x + e * kZThreads;
+            if (i < NH * NW) {
+                const int o = noff[e];
+                const float gx = (pc[o + 1] - pc[o - 1]) * 0.5f;
+                const float gy = (pc[o + PW] - pc[o - PW]) * 0.5f;
+                const float gz = (pp[o] - pm[o]) * 0.5f;
+                const float inv = rcp_approx(sqrt_approx(gx * gx + gy * gy + gz * gz) + 1e-10f);
+                n0[i] = gx * inv;
+                n1[i] = gy * inv;
+                n2[i] = gz * inv;
+            }
+        }
+    };
+
+    float pv[NPE];
+    for (int lz = z0 - 2; lz <= z0 + 3; ++lz) {
+        fetch_phi(lz, pv);
+        store_phi(lz, pv);
+    }
+    __syncthreads();
+    normals(z0 - 1);
+    normals(z0);
+    normals(z0 + 1);
+    fetch_phi(z0 + 3, pv);  // the first output step stores plane z0+3 again, from registers
+
+    const float pxy = active ? __ldg(B.prof + x) * __ldg(B.prof + nx + y) : 0.f;
+    const float *profz = B.prof + nx + ny;
+    const float l12 = B.lambda1 - B.lambda2, s2 = B.cs[2];
+    const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
+    const float eps = B.eps, eps_pi = eps * INV_PI, eps2 = eps * eps;
+    const float mu = B.mu, nu = B.nu, dt = B.dt;
+    const ImgT *img = reinterpret_cast<const ImgT *>(B.img);
+    long long qz = (long long)z0 * plane + col;  // this thread's voxel index at the output plane
+    float *phi_out = G.parity ? B.phi[0] : B.phi[1];
+    float *q_out = G.parity ? B.q[0] : B.q[1];
+
+    const float2 *src = B.abxy + (long long)min(y, ny - 1) * px + min(x, nx - 1);
+    auto load = [&](int s) -> float2 {
+        const int zi = z0 - R + s;
+        return (active && s < nsteps && (unsigned)zi < (unsigned)nz) ? __ldg(src + (long long)zi * pplane)
+                                                                      : make_float2(0.f, 0.f);
+    };
+    float2 r[M];
+#pragma unroll
+    for (int i = 0; i < kPFB; ++i) r[i] = load(i);
+    float iv = active ? centred(img, qz, inv_s, nms) : 0.f;
+    for (int base = 0; base < nsteps; base += M) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            const int s = base + j;
+            if (s < nsteps) {
+                r[(j + kPFB) % M] = load(s + kPFB);
+                if (s >= 2 * R) {
+                    const int zo = z0 + s - 2 * R;
+                    store_phi(zo + 3, pv);
+                    fetch_phi(zo + 4, pv);
+                    const float im = iv;
+                    if (active && zo + 1 < z1) iv = centred(img, qz + plane, inv_s, nms);
+                    __syncthreads();
+                    normals(zo + 2);
+                    if (active) {
+                        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int k = 0; k < T; ++k)
+                            acc = f2fma(make_float2(t.g[k], t.g[k]), r[(j - 2 * R + k + 2 * M) % M], acc);
+                        const float K1 = pxy * __ldg(profz + zo);
+                        const float g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
+                        const float *p0 = sphi[zo & 7];
+                        const int pc0 = (ty + 2) * PW + tx + 2;
+                        const float ph = p0[pc0];
+                        const float lap = (p0[pc0 + 1] + p0[pc0 - 1] - 2.f * ph) + (p0[pc0 + PW] + p0[pc0 - PW] - 2.f * ph) +
+                                          (sphi[(zo + 1) & 7][pc0] + sphi[(zo - 1) & 7][pc0] - 2.f * ph);
+                        const int nc0 = (ty + 1) * NW + tx + 1;
+                        const float *n0 = snrm[zo & 3][0], *n1 = snrm[zo & 3][1];
+                        const float kap = (n0[nc0 + 1] - n0[nc0 - 1]) * 0.5f + (n1[nc0 + NW] - n1[nc0 - NW]) * 0.5f +
+                                          (snrm[(zo + 1) & 3][2][nc0] - snrm[(zo - 1) & 3][2][nc0]) * 0.5f;
+                        const float del = eps_pi * rcp_approx(eps2 + ph * ph);  // Eq. (14)
+                        const float pn = ph + dt * (mu * (lap - kap) + del * (nu * kap - g));
+                        phi_out[qz] = pn;
+                        q_out[qz] = heaviside_q_fast(pn, eps);
+                        if (B.dump) {
+                            const long long n = (long long)nx * ny * nz;
+                            B.dump[2 * n + qz] = g;
+                            B.dump[3 * n + qz] = kap;
+                            B.dump[4 * n + qz] = lap;
+                        }
+                    }
+                    qz += plane;
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ launchers
+
+// The update kernel (storage independent; defined in rsf_tiled_f32.cu).
+cudaError_t launch_tb_z(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
+
+template <int R, class S>
+cudaError_t prepare_storage() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint8_t, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint16_t, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_ta_xy<R, float, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_ta_z<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)az_smem<R>())) !=
+        cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tb_xy<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)XYLayout<R, 1>::bytes);
+}
+
+template <int R, class S>
+cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    GroupArgs G{g.bricks, nullptr, g.nb, parity};
+    {
+        ProfScope ps(prof, KID_TA_XY);
+        G.starts = g.starts[0];
+        constexpr size_t sm = XYLayout<R, 2>::bytes;
+        switch (g.imgtype) {
+            case 0: k_ta_xy<R, uint8_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, g.taps); break;
+            case 1: k_ta_xy<R, uint16_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, g.taps); break;
+            default: k_ta_xy<R, float, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, g.taps);
+        }
+    }
+    {
+        ProfScope ps(prof, KID_TA_Z);
+        G.starts = g.starts[1];
+        k_ta_z<R, S><<<g.ncta[1], kAZThreads, az_smem<R>(), s>>>(G, g.taps);
+    }
+    {
+        ProfScope ps(prof, KID_TB_XY);
+        G.starts = g.starts[2];
+        constexpr size_t sm = XYLayout<R, 1>::bytes;
+        k_tb_xy<R, S><<<g.ncta[2], kXYThreads, sm, s>>>(G, g.taps);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_tb_z(g, parity, prof, s);
+}
+
+template <class S>
+cudaError_t prepare_group_s(int R) {
+    switch (R) {
+        case 2: return prepare_storage<2, S>();
+        case 3: return prepare_storage<3, S>();
+        case 4: return prepare_storage<4, S>();
+        case 5: return prepare_storage<5, S>();
+        case 6: return prepare_storage<6, S>();
+        case 8: return prepare_storage<8, S>();
+        case 10: return prepare_storage<10, S>();
+        case 12: return prepare_storage<12, S>();
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class S>
+cudaError_t launch_group_s(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    switch (g.taps.R) {
+        case 2: return launch_storage<2, S>(g, parity, prof, s);
+        case 3: return launch_storage<3, S>(g, parity, prof, s);
+        case 4: return launch_storage<4, S>(g, parity, prof, s);
+        case 5: return launch_storage<5, S>(g, parity, prof, s);
+        case 6: return launch_storage<6, S>(g, parity, prof, s);
+        case 8: return launch_storage<8, S>(g, parity, prof, s);
+        case 10: return launch_storage<10, S>(g, parity, prof, s);
+        case 12: return launch_storage<12, S>(g, parity, prof, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tiled
+}  // namespace rsf

@@ -1,0 +1,107 @@
+// rsf_tiled_f32.cu -- instantiates the tiled iteration with FP32 storage (see
+// rsf_tiled.cuh), the storage-independent update kernel, the q set-up kernel
+// and the host-side launch dispatch.
+#include "rsf_tiled.cuh"
+
+namespace rsf {
+namespace tiled {
+
+namespace {
+template <int R, class ImgT>
+cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    GroupArgs G{g.bricks, g.starts[3], g.nb, parity};
+    ProfScope ps(prof, KID_TB_Z);
+    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, 0, s>>>(G, g.taps);
+    return cudaGetLastError();
+}
+template <int R>
+cudaError_t launch_bz_i(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    switch (g.imgtype) {
+        case 0: return launch_bz_r<R, uint8_t>(g, parity, prof, s);
+        case 1: return launch_bz_r<R, uint16_t>(g, parity, prof, s);
+        default: return launch_bz_r<R, float>(g, parity, prof, s);
+    }
+}
+__global__ void k_q_init(const float *__restrict__ phi, float *__restrict__ q, long long n, float eps) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        q[i] = heaviside_q_fast(__ldg(phi + i), eps);
+}
+}  // namespace
+
+cudaError_t launch_tb_z(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    switch (g.taps.R) {
+        case 2: return launch_bz_i<2>(g, parity, prof, s);
+        case 3: return launch_bz_i<3>(g, parity, prof, s);
+        case 4: return launch_bz_i<4>(g, parity, prof, s);
+        case 5: return launch_bz_i<5>(g, parity, prof, s);
+        case 6: return launch_bz_i<6>(g, parity, prof, s);
+        case 8: return launch_bz_i<8>(g, parity, prof, s);
+        case 10: return launch_bz_i<10>(g, parity, prof, s);
+        case 12: return launch_bz_i<12>(g, parity, prof, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tiled
+
+bool tiled_supports(int R) {
+    switch (R) {
+        case 2: case 3: case 4: case 5: case 6: case 8: case 10: case 12: return true;
+        default: return false;
+    }
+}
+
+int tiled_pitch(int nx) { return (nx + tiled::kZX - 1) / tiled::kZX * tiled::kZX; }
+
+cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s) {
+    tiled::k_q_init<<<1216, 256, 0, s>>>(phi, q, n, eps);
+    return cudaGetLastError();
+}
+
+cudaError_t tiled_launch_f16(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
+cudaError_t tiled_launch_bf16(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
+cudaError_t tiled_prepare_f16(int R);
+cudaError_t tiled_prepare_bf16(int R);
+
+cudaError_t tiled_prepare(int storage, int R) {
+    switch (storage) {
+        case 0: return tiled::prepare_group_s<float>(R);
+        case 1: return tiled_prepare_bf16(R);
+        case 2: return tiled_prepare_f16(R);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    switch (g.storage) {
+        case 0: return tiled::launch_group_s<float>(g, parity, prof, s);
+        case 1: return tiled_launch_bf16(g, parity, prof, s);
+        case 2: return tiled_launch_f16(g, parity, prof, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+void tiled_cta_counts(const BrickDev &b, unsigned counts[4]) {
+    const unsigned ntx = (b.nx + tiled::kXYT - 1) / tiled::kXYT, nty = (b.ny + tiled::kXYT - 1) / tiled::kXYT;
+    const unsigned nzp = (b.nz + tiled::kXYPlanes - 1) / tiled::kXYPlanes;
+    counts[0] = ntx * nty * nzp;
+    counts[1] = (unsigned)((b.nz + tiled::kAZT - 1) / tiled::kAZT) * ((b.nx + 31) / 32) * b.ny;
+    counts[2] = counts[0];
+    counts[3] = (unsigned)((b.nx + tiled::kZX - 1) / tiled::kZX) * ((b.ny + tiled::kZY - 1) / tiled::kZY) *
+                ((b.nz + b.zc - 1) / b.zc);
+}
+
+size_t tiled_stage_bytes(int storage, long long np) {
+    const size_t e = storage == 0 ? 4 : 2;
+    return e * 4 * np + e * 2 * np + 8 * np;
+}
+
+void tiled_stage_views(int storage, void *base, long long np, void **u4, void **ab, float2 **abxy) {
+    const size_t e = storage == 0 ? 4 : 2;
+    char *p = static_cast<char *>(base);
+    *u4 = p;
+    *ab = p + e * 4 * np;
+    *abxy = reinterpret_cast<float2 *>(p + e * 6 * np);
+}
+
+}  // namespace rsf

@@ -28,8 +28,9 @@ EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_s
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option")
 
-OPT_PATH, OPT_ZCHUNK = 1, 2
+OPT_PATH, OPT_ZCHUNK, OPT_STORAGE = 1, 2, 3
 PATHS = {"auto": 0, "passes": 1, "tiled": 2}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 
 NOALLOC_MAX_VOXELS = 1 << 18
 
@@ -213,6 +214,10 @@ class Context:
     def set_path(self, name: str):
         """'auto' (tiled where instantiated, else passes), 'passes' or 'tiled'."""
         self.set_option(OPT_PATH, PATHS[name])
+
+    def set_storage(self, name: str):
+        """Storage of the intermediate fields: 'f32', 'bf16' or 'f16'."""
+        self.set_option(OPT_STORAGE, STORAGE[name])
 
     # kernel timing ---------------------------------------------------------
     def prof_enable(self, on: bool = True):
