@@ -98,6 +98,38 @@ rsf_status rsf_evolve(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx
                       float nu, float mu, float dt, int32_t iters);
 
 /*
+ * rsf_evolve_batch -- evolve `nbricks` independent bricks together.
+ *
+ * Each brick is a volume of its own (for example a halo-padded sub-volume of
+ * a larger image, the volume-level parallelism of Sec. 4.1) with its own
+ * parameters and iteration count; its result is the same as rsf_evolve on the
+ * same brick with the same context options (every voxel is computed by the
+ * same arithmetic in the same order).  All bricks start together and advance
+ * one iteration per step, one launch per kernel for each group of bricks that
+ * share a kernel radius and image type; a brick that has done its iterations
+ * retires and its phi is copied to its phi_out.  Between retirements the
+ * iteration is replayed from a captured CUDA graph (RSF_OPT_GRAPH).
+ *   bricks    array of nbricks descriptors (fields as in rsf_evolve); host or
+ *             device pointers; phi_out may alias phi0.
+ * Only the tiled kernels run batched: every brick's radius round(2 sigma) must
+ * be one of 2-6, 8, 10, 12.  Blocking.  Device memory for all bricks is taken
+ * at once from the context's HBM budget.
+ * Errors: RSF_E_INVAL (a brick's arguments, with its index in the message),
+ * RSF_E_NOMEM, RSF_E_CUDA.
+ */
+typedef struct {
+    const void *volume;
+    rsf_dtype vt;
+    int64_t nx, ny, nz;
+    const float *phi0;
+    float *phi_out;
+    float sigma, eps, lambda1, lambda2, nu, mu, dt;
+    int32_t iters;
+} rsf_brick;
+
+rsf_status rsf_evolve_batch(rsf_ctx *ctx, const rsf_brick *bricks, int32_t nbricks);
+
+/*
  * rsf_step_stages -- one iteration from phi with the intermediate fields
  * written out, for checking each stage against a reference.
  *   stages   host or device buffer of RSF_NSTAGES * nx*ny*nz floats,
@@ -135,12 +167,20 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   RSF_STORE_F16.  Accumulation is FP32 throughout; phi, the
  *                   image (read in its own type) and the x/y-convolved a, b
  *                   stay exact / FP32.  16-bit storage needs the tiled path.
+ *   RSF_OPT_AUTOTUNE 1: rsf_evolve_batch picks the update kernel's z chunk per
+ *                   brick group by timing candidates on a discarded first
+ *                   iteration and remembers the choice in the context; 0
+ *                   (default): a size heuristic.
+ *   RSF_OPT_GRAPH   1 (default): rsf_evolve_batch replays its iterations from
+ *                   a captured CUDA graph; 0: direct launches.
  * The paths give the same result per voxel up to the order of FP32 rounding.
  * Errors: RSF_E_INVAL (unknown key or value).
  */
 #define RSF_OPT_PATH 1
 #define RSF_OPT_ZCHUNK 2
 #define RSF_OPT_STORAGE 3
+#define RSF_OPT_AUTOTUNE 4
+#define RSF_OPT_GRAPH 5
 #define RSF_PATH_AUTO 0
 #define RSF_PATH_PASSES 1
 #define RSF_PATH_TILED 2

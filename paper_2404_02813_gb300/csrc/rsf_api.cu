@@ -13,13 +13,14 @@
 #include <vector>
 
 #include "rsf.h"
+#include "rsf_ctx.h"
 #include "rsf_internal.h"
 
 // ------------------------------------------------------------------ errors
 
 static thread_local std::string g_last_error;
 
-static rsf_status fail(rsf_status st, const char *fmt, ...) {
+rsf_status fail(rsf_status st, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -29,15 +30,11 @@ static rsf_status fail(rsf_status st, const char *fmt, ...) {
     return st;
 }
 
-static rsf_status cuda_fail(cudaError_t e, const char *what) {
+rsf_status cuda_fail(cudaError_t e, const char *what) {
     return fail(RSF_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-#define RSF_CUDA(call)                                             \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
-    } while (0)
+
 
 extern "C" const char *rsf_last_error(void) { return g_last_error.c_str(); }
 
@@ -95,33 +92,11 @@ void Profiler::release() {
 
 // ----------------------------------------------------------------- context
 
-struct rsf_ctx {
-    int device = 0;
-    uint64_t budget = 0;
-    uint64_t used = 0;
-    cudaStream_t stream = nullptr;
-    std::mutex mu;
-
-    rsf::Fields f;
-    long long cap_n = 0;     // elements per big field currently allocated
-    long long cap_np = 0;    // elements per stage field (pitched) currently allocated
-    long long cap_prof = 0;  // profile floats allocated
-    void *staging = nullptr; // device copy of a host volume
-    size_t staging_cap = 0;
-    float *dump = nullptr;   // device stage dump for host destinations
-    size_t dump_cap = 0;
-    rsf::Profiler prof;
-    int opt_path = RSF_PATH_AUTO;
-    int opt_zchunk = 0;
-    int opt_storage = RSF_STORE_F32;
-    rsf::BrickDev *d_bricks = nullptr;  // brick descriptors of the current launch group
-    int *d_starts = nullptr;            // 4 x (cap_bricks + 1) CTA offsets
-    int cap_bricks = 0;
-};
 
 
 
-static rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
+
+rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
     if (c->used + bytes > c->budget)
         return fail(RSF_E_NOMEM, "allocation of %zu bytes exceeds the HBM budget (%llu of %llu bytes in use)", bytes,
                     (unsigned long long)c->used, (unsigned long long)c->budget);
@@ -135,56 +110,70 @@ static rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
     return RSF_OK;
 }
 
-static void dev_free(rsf_ctx *c, void *p, size_t bytes) {
+void dev_free(rsf_ctx *c, void *p, size_t bytes) {
     if (!p) return;
     cudaFree(p);
     c->used -= std::min<uint64_t>(c->used, bytes);
 }
 
 
-// Copy `nb` brick descriptors and their per-kernel CTA offsets to the device
-// and describe them as one launch group.
-static rsf_status upload_group(rsf_ctx *c, const rsf::BrickDev *b, int nb, int storage, int imgtype,
-                               const rsf::Taps &taps, rsf::TiledGroup *g) {
-    if (nb > c->cap_bricks) {
+// Copy the brick descriptors of several launch groups and their per-kernel
+// CTA offsets to the device in one upload, and describe each group.
+rsf_status upload_groups(rsf_ctx *c, const std::vector<GroupSpec> &specs, std::vector<rsf::TiledGroup> *out) {
+    int total = 0;
+    for (const GroupSpec &g : specs) total += (int)g.bricks.size();
+    const int need_starts = 4 * (total + (int)specs.size());
+    if (total > c->cap_bricks || need_starts > c->cap_starts) {
         dev_free(c, c->d_bricks, sizeof(rsf::BrickDev) * (size_t)c->cap_bricks);
-        dev_free(c, c->d_starts, sizeof(int) * 4 * (size_t)(c->cap_bricks + 1));
+        dev_free(c, c->d_starts, sizeof(int) * (size_t)c->cap_starts);
         c->d_bricks = nullptr;
         c->d_starts = nullptr;
-        c->cap_bricks = 0;
-        const int cap = std::max(nb, 16);
+        c->cap_bricks = c->cap_starts = 0;
+        const int cap = std::max(total, 16), capst = std::max(need_starts, 4 * 32);
         rsf_status st = dev_alloc(c, (void **)&c->d_bricks, sizeof(rsf::BrickDev) * (size_t)cap);
         if (st) return st;
-        st = dev_alloc(c, (void **)&c->d_starts, sizeof(int) * 4 * (size_t)(cap + 1));
+        st = dev_alloc(c, (void **)&c->d_starts, sizeof(int) * (size_t)capst);
         if (st) return st;
         c->cap_bricks = cap;
+        c->cap_starts = capst;
     }
-    std::vector<int> starts(4 * (size_t)(nb + 1));
-    unsigned long long tot[4] = {0, 0, 0, 0};
-    for (int i = 0; i < nb; ++i) {
-        unsigned cnt[4];
-        rsf::tiled_cta_counts(b[i], cnt);
-        for (int k = 0; k < 4; ++k) {
-            starts[(size_t)k * (nb + 1) + i] = (int)tot[k];
-            tot[k] += cnt[k];
+    std::vector<rsf::BrickDev> all;
+    std::vector<int> starts;
+    all.reserve(total);
+    starts.reserve(need_starts);
+    out->clear();
+    for (const GroupSpec &gs : specs) {
+        const int nb = (int)gs.bricks.size();
+        rsf::TiledGroup g{};
+        g.storage = gs.storage;
+        g.imgtype = gs.imgtype;
+        g.taps = gs.taps;
+        g.bricks = c->d_bricks + all.size();
+        g.nb = nb;
+        const size_t s0 = starts.size();
+        starts.resize(s0 + 4 * (size_t)(nb + 1));
+        unsigned long long tot[4] = {0, 0, 0, 0};
+        for (int i = 0; i < nb; ++i) {
+            unsigned cnt[4];
+            rsf::tiled_cta_counts(gs.bricks[i], cnt);
+            for (int k = 0; k < 4; ++k) {
+                starts[s0 + (size_t)k * (nb + 1) + i] = (int)tot[k];
+                tot[k] += cnt[k];
+            }
         }
+        for (int k = 0; k < 4; ++k) {
+            if (tot[k] >= (1ull << 31)) return fail(RSF_E_INVAL, "launch group too large (%llu CTAs)", tot[k]);
+            starts[s0 + (size_t)k * (nb + 1) + nb] = (int)tot[k];
+            g.starts[k] = c->d_starts + s0 + (size_t)k * (nb + 1);
+            g.ncta[k] = (unsigned)tot[k];
+        }
+        all.insert(all.end(), gs.bricks.begin(), gs.bricks.end());
+        out->push_back(g);
     }
-    for (int k = 0; k < 4; ++k) {
-        if (tot[k] >= (1ull << 31)) return fail(RSF_E_INVAL, "launch group too large (%llu CTAs)", tot[k]);
-        starts[(size_t)k * (nb + 1) + nb] = (int)tot[k];
-    }
-    RSF_CUDA(cudaMemcpyAsync(c->d_bricks, b, sizeof(rsf::BrickDev) * nb, cudaMemcpyHostToDevice, c->stream));
+    RSF_CUDA(cudaMemcpyAsync(c->d_bricks, all.data(), sizeof(rsf::BrickDev) * all.size(), cudaMemcpyHostToDevice,
+                             c->stream));
     RSF_CUDA(cudaMemcpyAsync(c->d_starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice,
                              c->stream));
-    g->storage = storage;
-    g->imgtype = imgtype;
-    g->taps = taps;
-    g->bricks = c->d_bricks;
-    g->nb = nb;
-    for (int k = 0; k < 4; ++k) {
-        g->starts[k] = c->d_starts + (size_t)k * (nb + 1);
-        g->ncta[k] = (unsigned)tot[k];
-    }
     return RSF_OK;
 }
 
@@ -203,7 +192,7 @@ static void free_fields(rsf_ctx *c) {
     c->cap_prof = 0;
 }
 
-static rsf_status ensure_fields(rsf_ctx *c, int nx, int ny, int nz) {
+rsf_status ensure_fields(rsf_ctx *c, int nx, int ny, int nz) {
     rsf::Dims d{nx, ny, nz, (long long)nx * ny, (long long)nx * ny * nz};
     const int px = rsf::tiled_pitch(nx);
     const long long np = (long long)px * ny * nz;  // >= n: also holds the pass path's fields
@@ -249,7 +238,7 @@ static rsf_status ensure_fields(rsf_ctx *c, int nx, int ny, int nz) {
 }
 
 // True when p is memory the device can use in place (device or managed).
-static bool on_device(const void *p) {
+bool on_device(const void *p) {
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) {
@@ -259,7 +248,7 @@ static bool on_device(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static size_t dtype_size(rsf_dtype vt) { return vt == RSF_U8 ? 1 : (vt == RSF_U16 ? 2 : 4); }
+size_t dtype_size(rsf_dtype vt) { return vt == RSF_U8 ? 1 : (vt == RSF_U16 ? 2 : 4); }
 
 // Device-resident copy of the volume (the caller's own pointer when it already is one).
 static rsf_status device_volume(rsf_ctx *c, const void *volume, rsf_dtype vt, long long n, const void **out) {
@@ -281,7 +270,7 @@ static rsf_status device_volume(rsf_ctx *c, const void *volume, rsf_dtype vt, lo
     return RSF_OK;
 }
 
-static rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz, const void *phi0,
+rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz, const void *phi0,
                              const void *phi_out, float sigma, float eps, float dt, int32_t iters) {
     if (!volume || !phi0 || !phi_out) return fail(RSF_E_INVAL, "null volume, phi0 or phi_out pointer");
     if (vt != RSF_U8 && vt != RSF_U16 && vt != RSF_F32) return fail(RSF_E_INVAL, "unknown volume dtype %d", (int)vt);
@@ -303,7 +292,7 @@ static rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64
 }
 
 // Normalised taps of Eq. (7): exp(-k^2/(2 sigma^2)) / sum, R = round(2 sigma).
-static rsf::Taps make_taps(float sigma) {
+rsf::Taps make_taps(float sigma) {
     rsf::Taps t{};
     t.R = (int)std::floor(2.0 * (double)sigma + 0.5);
     double w[2 * rsf::RMAX + 1], s = 0.0;
@@ -352,7 +341,8 @@ extern "C" void rsf_destroy(rsf_ctx *c) {
         dev_free(c, c->staging, c->staging_cap);
         dev_free(c, c->dump, c->dump_cap);
         dev_free(c, c->d_bricks, sizeof(rsf::BrickDev) * (size_t)c->cap_bricks);
-        dev_free(c, c->d_starts, sizeof(int) * 4 * (size_t)(c->cap_bricks + 1));
+        dev_free(c, c->d_starts, sizeof(int) * (size_t)c->cap_starts);
+        dev_free(c, c->pool, c->pool_cap);
         c->prof.release();
         cudaStreamDestroy(c->stream);
     }
@@ -434,8 +424,14 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
             b.zc = (int)std::max<long long>(16, (nz + chunks - 1) / chunks);
         }
         b.dump = dump;  // only rsf_step_stages asks for stages, and it runs one iteration
-        rsf::TiledGroup g{};
-        if ((st = upload_group(c, &b, 1, storage, (int)vt, taps, &g))) return st;
+        std::vector<GroupSpec> specs(1);
+        specs[0].storage = storage;
+        specs[0].imgtype = (int)vt;
+        specs[0].taps = taps;
+        specs[0].bricks.push_back(b);
+        std::vector<rsf::TiledGroup> groups;
+        if ((st = upload_groups(c, specs, &groups))) return st;
+        const rsf::TiledGroup &g = groups[0];
         if (iters > 0) RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
         for (int it = 0; it < iters; ++it) {
             cudaError_t e = rsf::tiled_iterate(g, it & 1, &c->prof, c->stream);
@@ -497,6 +493,12 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
             if (value != RSF_STORE_F32 && value != RSF_STORE_BF16 && value != RSF_STORE_F16)
                 return fail(RSF_E_INVAL, "unknown storage %lld", (long long)value);
             c->opt_storage = (int)value;
+            return RSF_OK;
+        case RSF_OPT_AUTOTUNE:
+            c->opt_autotune = value != 0;
+            return RSF_OK;
+        case RSF_OPT_GRAPH:
+            c->opt_graph = value != 0;
             return RSF_OK;
         case RSF_OPT_ZCHUNK:
             if (value < 0 || value > (1 << 20)) return fail(RSF_E_INVAL, "z chunk must lie in [0, 2^20]");

@@ -1,0 +1,67 @@
+// rsf_ctx.h -- the context behind the C ABI's opaque rsf_ctx and the host
+// helpers shared by the translation units of the C ABI (rsf_api.cu,
+// rsf_batch.cu).  Not installed; not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rsf.h"
+#include "rsf_internal.h"
+
+struct rsf_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    cudaStream_t stream = nullptr;
+    std::mutex mu;
+
+    rsf::Fields f;
+    long long cap_n = 0;     // elements per big field currently allocated
+    long long cap_np = 0;    // elements per stage field (pitched) currently allocated
+    long long cap_prof = 0;  // profile floats allocated
+    void *staging = nullptr; // device copy of a host volume
+    size_t staging_cap = 0;
+    float *dump = nullptr;   // device stage dump for host destinations
+    size_t dump_cap = 0;
+    rsf::Profiler prof;
+    int opt_path = RSF_PATH_AUTO;
+    int opt_zchunk = 0;
+    int opt_storage = RSF_STORE_F32;
+    rsf::BrickDev *d_bricks = nullptr;  // brick descriptors of the current launch groups
+    int *d_starts = nullptr;            // per group: 4 x (nb + 1) CTA offsets
+    int cap_bricks = 0, cap_starts = 0;
+    int opt_autotune = 0;
+    int opt_graph = 1;
+    void *pool = nullptr;               // per-brick fields of rsf_evolve_batch
+    size_t pool_cap = 0;
+    std::map<std::string, int> tuned_zc;  // autotuned update-kernel z chunk per group key
+};
+
+// One launch group before upload: bricks sharing radius, image type, storage.
+struct GroupSpec {
+    int storage = 0, imgtype = 0;
+    rsf::Taps taps{};
+    std::vector<rsf::BrickDev> bricks;
+};
+
+rsf_status fail(rsf_status st, const char *fmt, ...);
+rsf_status cuda_fail(cudaError_t e, const char *what);
+#define RSF_CUDA(call)                                             \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes);
+void dev_free(rsf_ctx *c, void *p, size_t bytes);
+bool on_device(const void *p);
+size_t dtype_size(rsf_dtype vt);
+rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz, const void *phi0,
+                      const void *phi_out, float sigma, float eps, float dt, int32_t iters);
+rsf::Taps make_taps(float sigma);
+rsf_status upload_groups(rsf_ctx *c, const std::vector<GroupSpec> &specs, std::vector<rsf::TiledGroup> *out);

@@ -26,13 +26,22 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
-            "rsf_set_option")
+            "rsf_set_option", "rsf_evolve_batch")
 
-OPT_PATH, OPT_ZCHUNK, OPT_STORAGE = 1, 2, 3
+OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH = 1, 2, 3, 4, 5
 PATHS = {"auto": 0, "passes": 1, "tiled": 2}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 
 NOALLOC_MAX_VOXELS = 1 << 18
+
+
+class Brick(ctypes.Structure):
+    """rsf_brick (include/rsf.h)."""
+    _fields_ = [("volume", ctypes.c_void_p), ("vt", ctypes.c_int32), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("nz", ctypes.c_int64), ("phi0", ctypes.c_void_p), ("phi_out", ctypes.c_void_p),
+                ("sigma", ctypes.c_float), ("eps", ctypes.c_float), ("lambda1", ctypes.c_float),
+                ("lambda2", ctypes.c_float), ("nu", ctypes.c_float), ("mu", ctypes.c_float), ("dt", ctypes.c_float),
+                ("iters", ctypes.c_int32)]
 
 
 class RSFError(RuntimeError):
@@ -73,6 +82,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_prof_get.restype = i32
     L.rsf_evolve_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, vp]
     L.rsf_evolve_noalloc.restype = i32
+    L.rsf_evolve_batch.argtypes = [vp, ctypes.POINTER(Brick), i32]
+    L.rsf_evolve_batch.restype = i32
     L.rsf_set_option.argtypes = [vp, i32, i64]
     L.rsf_set_option.restype = i32
     L.rsf_last_error.argtypes = []
@@ -214,6 +225,24 @@ class Context:
     def set_path(self, name: str):
         """'auto' (tiled where instantiated, else passes), 'passes' or 'tiled'."""
         self.set_option(OPT_PATH, PATHS[name])
+
+    def evolve_batch(self, items):
+        """rsf_evolve_batch over (volume, phi0, params, iters[, out]) tuples; returns the outputs."""
+        arr = (Brick * len(items))()
+        outs, keep = [], []
+        for k, it in enumerate(items):
+            volume, phi0, params, iters = it[:4]
+            out = it[4] if len(it) > 4 else (phi0.clone() if hasattr(phi0, "clone") else np.empty_like(phi0))
+            p = Params.of(params)
+            nz, ny, nx = _shape(volume)
+            if _shape(phi0) != (nz, ny, nx) or _shape(out) != (nz, ny, nx):
+                raise ValueError(f"brick {k}: shapes differ")
+            arr[k] = Brick(_ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0), _ptr(out), *p.tuple(), int(iters))
+            outs.append(out)
+            keep.append((volume, phi0))
+        _order_after_caller(*[x for pair in keep for x in pair], *outs)
+        _check(load_library().rsf_evolve_batch(self._h, arr, len(items)))
+        return outs
 
     def set_storage(self, name: str):
         """Storage of the intermediate fields: 'f32', 'bf16' or 'f16'."""
