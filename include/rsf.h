@@ -173,6 +173,10 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   (default): a size heuristic.
  *   RSF_OPT_GRAPH   1 (default): rsf_evolve_batch replays its iterations from
  *                   a captured CUDA graph; 0: direct launches.
+ *   RSF_OPT_FAULT_ADMISSION  k > 0: the serving loop fails the set-up of its
+ *                   k-th admission with RSF_E_CUDA, on the host, without any
+ *                   device work (for testing failure handling); 0: off.  Read
+ *                   when the serving loop starts (the first rsf_submit).
  * The paths give the same result per voxel up to the order of FP32 rounding.
  * Errors: RSF_E_INVAL (unknown key or value).
  */
@@ -181,10 +185,74 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 #define RSF_OPT_STORAGE 3
 #define RSF_OPT_AUTOTUNE 4
 #define RSF_OPT_GRAPH 5
+#define RSF_OPT_FAULT_ADMISSION 6
 #define RSF_PATH_AUTO 0
 #define RSF_PATH_PASSES 1
 #define RSF_PATH_TILED 2
 rsf_status rsf_set_option(rsf_ctx *ctx, int32_t key, int64_t value);
+
+/*
+ * Serving: continuous batching of brick requests (no counterpart in the
+ * paper's method beyond its independent sub-volumes, Sec. 4.1).
+ *
+ * rsf_submit queues a request and returns at once with a ticket.  A
+ * scheduler thread of the context admits queued requests in arrival order
+ * while their device footprint fits the context's HBM budget, keeps every
+ * admitted brick's phi and working fields resident on the device, and
+ * advances all admitted bricks together one iteration per step (continuous
+ * batching: a request admitted while others run joins at the next step; a
+ * brick that has done its iterations leaves at once and frees its memory for
+ * the next admission).  Each brick's result is the same as rsf_evolve on that
+ * brick with the same storage.
+ *   volume, phi0, phi_out  host or device pointers; the caller keeps them
+ *            valid and unchanged until the ticket is no longer pending.
+ *            Host images are copied at admission; pinned host memory keeps
+ *            that copy asynchronous.
+ *   storage  RSF_STORE_F32 / BF16 / F16 for this brick's intermediate fields.
+ *   halo     the padding already included in nx, ny, nz on each side (for the
+ *            caller's bookkeeping; -1 = 3 sigma); it must leave a core.
+ *   stream   NULL, or a cudaStream_t whose work queued before admission must
+ *            finish before the brick's inputs are read.
+ * Errors of rsf_submit: RSF_E_INVAL (arguments), RSF_E_NOMEM (the request
+ * alone exceeds the HBM budget), RSF_E_BUSY (queue full).
+ *
+ * rsf_poll returns RSF_PENDING, or the request's final status (RSF_OK,
+ * RSF_E_CANCELLED, RSF_E_NOMEM, RSF_E_CUDA) together with its latency from
+ * submission to completion in seconds (nullable); a ticket is released by the
+ * first poll that returns a final status (later polls: RSF_E_NOTFOUND).
+ * rsf_wait blocks up to timeout_ms (< 0: no limit) for a final status, then
+ * behaves as rsf_poll; on expiry it returns RSF_E_TIMEOUT and keeps the ticket.
+ * rsf_cancel marks a request cancelled: it leaves the queue, or the batch at
+ * the next step, and its phi_out is not written.
+ * rsf_serve_stats reports counts, completed voxel-iterations, the busy time
+ * from the first submission to the last completion, and latency percentiles
+ * of the completed requests.
+ */
+typedef struct {
+    const void *volume;
+    rsf_dtype vt;
+    int64_t nx, ny, nz;
+    const float *phi0;
+    float *phi_out;
+    float sigma, eps, lambda1, lambda2, nu, mu, dt;
+    int32_t iters;
+    rsf_storage storage;
+    int32_t halo;
+    void *stream;
+} rsf_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled, queued;
+    double voxel_iterations;
+    double busy_s;
+    double latency_p50_s, latency_p99_s, latency_max_s;
+} rsf_serve_stat;
+
+rsf_status rsf_submit(rsf_ctx *ctx, const rsf_request *req, uint64_t *ticket);
+rsf_status rsf_poll(rsf_ctx *ctx, uint64_t ticket, double *latency_s);
+rsf_status rsf_wait(rsf_ctx *ctx, uint64_t ticket, int32_t timeout_ms);
+rsf_status rsf_cancel(rsf_ctx *ctx, uint64_t ticket);
+rsf_status rsf_serve_stats(rsf_ctx *ctx, rsf_serve_stat *out);
 
 /*
  * Kernel timing.  While enabled, the context records a CUDA event pair on its

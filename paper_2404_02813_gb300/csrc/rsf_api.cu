@@ -97,6 +97,7 @@ void Profiler::release() {
 
 
 rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
     if (c->used + bytes > c->budget)
         return fail(RSF_E_NOMEM, "allocation of %zu bytes exceeds the HBM budget (%llu of %llu bytes in use)", bytes,
                     (unsigned long long)c->used, (unsigned long long)c->budget);
@@ -112,6 +113,7 @@ rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes) {
 
 void dev_free(rsf_ctx *c, void *p, size_t bytes) {
     if (!p) return;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
     cudaFree(p);
     c->used -= std::min<uint64_t>(c->used, bytes);
 }
@@ -119,23 +121,26 @@ void dev_free(rsf_ctx *c, void *p, size_t bytes) {
 
 // Copy the brick descriptors of several launch groups and their per-kernel
 // CTA offsets to the device in one upload, and describe each group.
-rsf_status upload_groups(rsf_ctx *c, const std::vector<GroupSpec> &specs, std::vector<rsf::TiledGroup> *out) {
+void free_desc(rsf_ctx *c, DescBuffers &buf) {
+    dev_free(c, buf.d_bricks, sizeof(rsf::BrickDev) * (size_t)buf.cap_bricks);
+    dev_free(c, buf.d_starts, sizeof(int) * (size_t)buf.cap_starts);
+    buf = DescBuffers{};
+}
+
+rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, const std::vector<GroupSpec> &specs,
+                         std::vector<rsf::TiledGroup> *out) {
     int total = 0;
     for (const GroupSpec &g : specs) total += (int)g.bricks.size();
     const int need_starts = 4 * (total + (int)specs.size());
-    if (total > c->cap_bricks || need_starts > c->cap_starts) {
-        dev_free(c, c->d_bricks, sizeof(rsf::BrickDev) * (size_t)c->cap_bricks);
-        dev_free(c, c->d_starts, sizeof(int) * (size_t)c->cap_starts);
-        c->d_bricks = nullptr;
-        c->d_starts = nullptr;
-        c->cap_bricks = c->cap_starts = 0;
+    if (total > buf.cap_bricks || need_starts > buf.cap_starts) {
+        free_desc(c, buf);
         const int cap = std::max(total, 16), capst = std::max(need_starts, 4 * 32);
-        rsf_status st = dev_alloc(c, (void **)&c->d_bricks, sizeof(rsf::BrickDev) * (size_t)cap);
+        rsf_status st = dev_alloc(c, (void **)&buf.d_bricks, sizeof(rsf::BrickDev) * (size_t)cap);
         if (st) return st;
-        st = dev_alloc(c, (void **)&c->d_starts, sizeof(int) * (size_t)capst);
+        st = dev_alloc(c, (void **)&buf.d_starts, sizeof(int) * (size_t)capst);
         if (st) return st;
-        c->cap_bricks = cap;
-        c->cap_starts = capst;
+        buf.cap_bricks = cap;
+        buf.cap_starts = capst;
     }
     std::vector<rsf::BrickDev> all;
     std::vector<int> starts;
@@ -148,7 +153,7 @@ rsf_status upload_groups(rsf_ctx *c, const std::vector<GroupSpec> &specs, std::v
         g.storage = gs.storage;
         g.imgtype = gs.imgtype;
         g.taps = gs.taps;
-        g.bricks = c->d_bricks + all.size();
+        g.bricks = buf.d_bricks + all.size();
         g.nb = nb;
         const size_t s0 = starts.size();
         starts.resize(s0 + 4 * (size_t)(nb + 1));
@@ -164,16 +169,16 @@ rsf_status upload_groups(rsf_ctx *c, const std::vector<GroupSpec> &specs, std::v
         for (int k = 0; k < 4; ++k) {
             if (tot[k] >= (1ull << 31)) return fail(RSF_E_INVAL, "launch group too large (%llu CTAs)", tot[k]);
             starts[s0 + (size_t)k * (nb + 1) + nb] = (int)tot[k];
-            g.starts[k] = c->d_starts + s0 + (size_t)k * (nb + 1);
+            g.starts[k] = buf.d_starts + s0 + (size_t)k * (nb + 1);
             g.ncta[k] = (unsigned)tot[k];
         }
         all.insert(all.end(), gs.bricks.begin(), gs.bricks.end());
         out->push_back(g);
     }
-    RSF_CUDA(cudaMemcpyAsync(c->d_bricks, all.data(), sizeof(rsf::BrickDev) * all.size(), cudaMemcpyHostToDevice,
-                             c->stream));
-    RSF_CUDA(cudaMemcpyAsync(c->d_starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice,
-                             c->stream));
+    RSF_CUDA(cudaMemcpyAsync(buf.d_bricks, all.data(), sizeof(rsf::BrickDev) * all.size(), cudaMemcpyHostToDevice,
+                             stream));
+    RSF_CUDA(cudaMemcpyAsync(buf.d_starts, starts.data(), sizeof(int) * starts.size(), cudaMemcpyHostToDevice,
+                             stream));
     return RSF_OK;
 }
 
@@ -330,6 +335,7 @@ extern "C" rsf_status rsf_create(rsf_ctx **out, int device, uint64_t hbm_budget_
 
 extern "C" void rsf_destroy(rsf_ctx *c) {
     if (!c) return;
+    rsf_serve_shutdown(c);
     {
         std::lock_guard<std::mutex> lk(c->mu);
         cudaSetDevice(c->device);
@@ -340,8 +346,7 @@ extern "C" void rsf_destroy(rsf_ctx *c) {
         dev_free(c, c->f.err, sizeof(int));
         dev_free(c, c->staging, c->staging_cap);
         dev_free(c, c->dump, c->dump_cap);
-        dev_free(c, c->d_bricks, sizeof(rsf::BrickDev) * (size_t)c->cap_bricks);
-        dev_free(c, c->d_starts, sizeof(int) * (size_t)c->cap_starts);
+        free_desc(c, c->desc);
         dev_free(c, c->pool, c->pool_cap);
         c->prof.release();
         cudaStreamDestroy(c->stream);
@@ -430,7 +435,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         specs[0].taps = taps;
         specs[0].bricks.push_back(b);
         std::vector<rsf::TiledGroup> groups;
-        if ((st = upload_groups(c, specs, &groups))) return st;
+        if ((st = upload_groups(c, c->desc, c->stream, specs, &groups))) return st;
         const rsf::TiledGroup &g = groups[0];
         if (iters > 0) RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
         for (int it = 0; it < iters; ++it) {
@@ -493,6 +498,10 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
             if (value != RSF_STORE_F32 && value != RSF_STORE_BF16 && value != RSF_STORE_F16)
                 return fail(RSF_E_INVAL, "unknown storage %lld", (long long)value);
             c->opt_storage = (int)value;
+            return RSF_OK;
+        case RSF_OPT_FAULT_ADMISSION:
+            if (value < 0) return fail(RSF_E_INVAL, "fault admission index must be >= 0");
+            c->opt_inject_admission = value;
             return RSF_OK;
         case RSF_OPT_AUTOTUNE:
             c->opt_autotune = value != 0;

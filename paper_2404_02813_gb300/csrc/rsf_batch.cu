@@ -107,7 +107,7 @@ rsf_status autotune_zc(rsf_ctx *c, GroupSpec &g, int sms) {
         set_zc(g, zc);
         std::vector<GroupSpec> one{g};
         std::vector<rsf::TiledGroup> up;
-        rsf_status st = upload_groups(c, one, &up);
+        rsf_status st = upload_groups(c, c->desc, c->stream, one, &up);
         if (st) return st;
         for (int rep = 0; rep < 2; ++rep) {  // first launch warms caches and attributes
             RSF_CUDA(cudaEventRecord(e0, c->stream));
@@ -273,7 +273,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         }
         tuned_once = true;
         std::vector<rsf::TiledGroup> groups;
-        if ((st = upload_groups(c, specs, &groups))) return st;
+        if ((st = upload_groups(c, c->desc, c->stream, specs, &groups))) return st;
         int steps = t_next - t;
         rsf::Profiler *prof = c->prof.on ? &c->prof : nullptr;
         if (c->opt_graph && !prof && steps >= 4) {

@@ -14,6 +14,13 @@
 #include "rsf.h"
 #include "rsf_internal.h"
 
+// Device copies of launch-group descriptors, owned by one user of the tiled kernels.
+struct DescBuffers {
+    rsf::BrickDev *d_bricks = nullptr;  // descriptors of every group of the last upload
+    int *d_starts = nullptr;            // per group: 4 x (nb + 1) CTA offsets
+    int cap_bricks = 0, cap_starts = 0;
+};
+
 struct rsf_ctx {
     int device = 0;
     uint64_t budget = 0;
@@ -33,14 +40,16 @@ struct rsf_ctx {
     int opt_path = RSF_PATH_AUTO;
     int opt_zchunk = 0;
     int opt_storage = RSF_STORE_F32;
-    rsf::BrickDev *d_bricks = nullptr;  // brick descriptors of the current launch groups
-    int *d_starts = nullptr;            // per group: 4 x (nb + 1) CTA offsets
-    int cap_bricks = 0, cap_starts = 0;
+    DescBuffers desc;                   // brick descriptors of rsf_evolve / rsf_evolve_batch launches
     int opt_autotune = 0;
     int opt_graph = 1;
     void *pool = nullptr;               // per-brick fields of rsf_evolve_batch
     size_t pool_cap = 0;
     std::map<std::string, int> tuned_zc;  // autotuned update-kernel z chunk per group key
+    std::mutex alloc_mu;                // guards `used` (the serving thread allocates too)
+    std::mutex serve_mu;                // guards creation of the serving loop
+    void *server = nullptr;             // the serving loop (rsf_serve.cu), created by rsf_submit
+    int64_t opt_inject_admission = 0;   // host-side fault injection for the serving loop
 };
 
 // One launch group before upload: bricks sharing radius, image type, storage.
@@ -64,4 +73,7 @@ size_t dtype_size(rsf_dtype vt);
 rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz, const void *phi0,
                       const void *phi_out, float sigma, float eps, float dt, int32_t iters);
 rsf::Taps make_taps(float sigma);
-rsf_status upload_groups(rsf_ctx *c, const std::vector<GroupSpec> &specs, std::vector<rsf::TiledGroup> *out);
+rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t s, const std::vector<GroupSpec> &specs,
+                         std::vector<rsf::TiledGroup> *out);
+void free_desc(rsf_ctx *c, DescBuffers &buf);
+void rsf_serve_shutdown(rsf_ctx *c);

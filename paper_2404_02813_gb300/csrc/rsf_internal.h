@@ -76,6 +76,12 @@ constexpr int kErrTimeout = 1;  // value of Fields::err after an expired bounded
 // centred image f.I.  `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
 cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s, bool centre = true);
 
+// Centring constants only (f.cs from the image statistics), no other field.
+cudaError_t image_stats(const void *vol, int vt, Fields &f, cudaStream_t s);
+// Zero-padding profiles p_a(i) = sum of the in-volume taps (double sums rounded
+// once), nx + ny + nz floats: K*1 = p_x p_y p_z.
+void zero_padding_profiles(const Taps &taps, int nx, int ny, int nz, float *out);
+
 // The centring half of setup_image alone (statistics and centred image, no
 // profiles); enqueues on `s` and never synchronises.
 cudaError_t centre_image(const void *vol, int vt, Fields &f, cudaStream_t s);
@@ -95,6 +101,7 @@ struct BrickDev {
     float2 *abxy;           // pitched x/y-convolved (a, b), FP32
     float eps, lambda1, lambda2, nu, mu, dt;
     int zc;                 // z chunk of the update kernel
+    int flip;               // this brick's buffer parity is the launch parity xor flip
     float *dump;            // optional 5 * n stage fields (f1, f2, g, kappa, L)
 };
 

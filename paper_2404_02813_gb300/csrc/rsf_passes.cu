@@ -277,6 +277,30 @@ static void launch_s(Outs<NF> in, Epi epi, const Dims &d, const Taps &t, int axi
     k_spass<NF, Epi><<<grid, dim3(kSX, kSY), 0, s>>>(in, epi, d, t, axis);
 }
 
+void zero_padding_profiles(const Taps &taps, int nx, int ny, int nz, float *out) {
+    // p_a(i) = sum_{k: 0 <= i+k < n_a} g[k], summed in double: K*1 = p_x p_y p_z
+    const int n3[3] = {nx, ny, nz};
+    size_t o = 0;
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < n3[a]; ++i) {
+            double acc = 0.0;
+            for (int k = -taps.R; k <= taps.R; ++k)
+                if (i + k >= 0 && i + k < n3[a]) acc += (double)taps.g[k + taps.R];
+            out[o++] = (float)acc;
+        }
+}
+
+cudaError_t image_stats(const void *vol, int vt, Fields &f, cudaStream_t s) {
+    const Dims &d = f.d;
+    switch (vt) {
+        case 0: k_stats<uint8_t><<<kStatBlocks, 256, 0, s>>>((const uint8_t *)vol, d.n, f.partials); break;
+        case 1: k_stats<uint16_t><<<kStatBlocks, 256, 0, s>>>((const uint16_t *)vol, d.n, f.partials); break;
+        default: k_stats<float><<<kStatBlocks, 256, 0, s>>>((const float *)vol, d.n, f.partials);
+    }
+    k_stats_final<<<1, kStatBlocks, 0, s>>>(f.partials, d.n, f.cs);
+    return cudaGetLastError();
+}
+
 cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cudaStream_t s, bool centre) {
     const Dims &d = f.d;
     const int eb = 1184;  // elementwise grid: a multiple of the SM count, grid-stride beyond
@@ -298,17 +322,8 @@ cudaError_t setup_image(const void *vol, int vt, const Taps &taps, Fields &f, cu
             default: k_center<float><<<eb, 256, 0, s>>>((const float *)vol, d.n, f.cs, f.I);
         }
     }
-    // zero-padding profiles p_a(i) = sum_{k: 0 <= i+k < n_a} g[k]: K*1 = p_x p_y p_z
     std::vector<float> prof((size_t)d.nx + d.ny + d.nz);
-    const int n3[3] = {d.nx, d.ny, d.nz};
-    size_t o = 0;
-    for (int a = 0; a < 3; ++a)
-        for (int i = 0; i < n3[a]; ++i) {
-            double acc = 0.0;
-            for (int k = -taps.R; k <= taps.R; ++k)
-                if (i + k >= 0 && i + k < n3[a]) acc += (double)taps.g[k + taps.R];
-            prof[o++] = (float)acc;
-        }
+    zero_padding_profiles(taps, d.nx, d.ny, d.nz, prof.data());
     cudaError_t e = cudaMemcpyAsync(f.prof, prof.data(), sizeof(float) * prof.size(), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     // the pageable source must stay alive until the copy has been consumed

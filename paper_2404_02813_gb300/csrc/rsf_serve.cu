@@ -1,0 +1,549 @@
+// rsf_serve.cu -- the request loop behind rsf_submit / rsf_poll / rsf_wait /
+// rsf_cancel: continuous batching of brick segmentation requests at iteration
+// granularity.
+//
+// A scheduler thread per context runs "ticks".  Before each tick it admits
+// queued requests in arrival order while their device footprint fits the
+// context's HBM budget: the brick's fields are allocated from the stream-
+// ordered pool, its image statistics, K*1 profiles, phi0 and q are prepared on
+// a set-up stream, and the compute stream waits on that work.  A tick is one
+// iteration of every active brick -- one launch per kernel for each group of
+// bricks sharing a kernel radius, image type and storage (the batched kernels
+// of rsf_evolve_batch); a brick admitted at tick T0 runs its iteration k at
+// tick T0 + k (its buffer parity is flipped accordingly).  A brick that has
+// done its iterations (or was cancelled) retires at once: its phi is copied to
+// the caller's phi_out, a host callback stamps its completion time, and its
+// memory returns to the pool in stream order, so the next admission can use
+// it.  The loop runs at most a few ticks ahead of the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "rsf.h"
+#include "rsf_ctx.h"
+#include "rsf_internal.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
+
+constexpr size_t kMaxQueue = 1 << 20;
+constexpr int kMaxAhead = 3;          // ticks the loop may run ahead of the GPU
+constexpr int kParamChunk = 6144;      // floats per parameter upload launch
+
+struct ParamChunk {
+    int offset, count;
+    float v[kParamChunk];
+};
+
+__global__ void k_put(ParamChunk c, float *__restrict__ dst) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.count; i += gridDim.x * blockDim.x)
+        dst[c.offset + i] = c.v[i];
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Request {
+    uint64_t ticket = 0;
+    rsf_request req{};
+    double t_submit = 0.0;
+    std::atomic<int> status{RSF_PENDING};
+    std::atomic<bool> cancel{false};
+    double t_done = 0.0;
+    // set at admission
+    rsf::BrickDev d{};
+    rsf::Taps taps{};
+    int imgtype = 0, storage = 0;
+    long long n = 0;
+    size_t bytes = 0;
+    void *mem = nullptr;
+    int done_iters = 0;
+    cudaEvent_t ready = nullptr;
+};
+
+struct Server;
+
+struct DoneArg {
+    Server *srv;
+    std::shared_ptr<Request> r;
+    int status;
+};
+
+struct Server {
+    rsf_ctx *ctx = nullptr;
+    std::thread th;
+    std::mutex mu;                   // queue, tickets, stop, stats
+    std::condition_variable cv;      // work for the scheduler
+    std::condition_variable done_cv; // completions for rsf_wait
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> tickets;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    // scheduler-thread state
+    std::vector<std::shared_ptr<Request>> active;
+    cudaStream_t s_comp = nullptr, s_setup = nullptr;
+    float *partials = nullptr;
+    uint64_t tick = 0;
+    std::deque<cudaEvent_t> inflight;
+    bool groups_dirty = true;
+    std::vector<rsf::TiledGroup> groups;
+    DescBuffers desc;
+    int sms = 0;
+    // statistics (mu)
+    uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, admitted = 0;
+    double vox_iters = 0.0, t_first = 0.0, t_last = 0.0;
+    std::vector<double> latencies;
+    // host-side fault injection: the k-th admission (1-based) fails its set-up
+    int64_t inject_admission = 0;
+};
+
+void CUDART_CB done_cb(void *p) {
+    DoneArg *a = static_cast<DoneArg *>(p);
+    Server *s = a->srv;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        a->r->t_done = now_s();
+        a->r->status.store(a->status);
+        if (a->status == RSF_OK) {
+            ++s->completed;
+            s->latencies.push_back(a->r->t_done - a->r->t_submit);
+            s->vox_iters += (double)a->r->n * a->r->req.iters;
+            s->t_last = a->r->t_done;
+        } else if (a->status == RSF_E_CANCELLED) {
+            ++s->cancelled;
+        } else {
+            ++s->failed;
+        }
+    }
+    s->done_cv.notify_all();
+    delete a;
+}
+
+// Device bytes of one served brick: phi and q pairs, profiles, centring
+// constants, the pitched intermediate fields and (host images) a device copy.
+size_t footprint(const rsf_request &r, bool stage_image) {
+    const long long n = (long long)r.nx * r.ny * r.nz;
+    const long long np = (long long)rsf::tiled_pitch((int)r.nx) * r.ny * r.nz;
+    size_t b = 4 * align256(sizeof(float) * n) + align256(sizeof(float) * (r.nx + r.ny + r.nz)) + align256(64);
+    b += align256(rsf::tiled_stage_bytes((int)r.storage, np));
+    if (stage_image) b += align256(dtype_size(r.vt) * n);
+    return b;
+}
+
+// Finish a request that never became active (or failed in set-up).
+void finish_now(Server *s, const std::shared_ptr<Request> &r, int status) {
+    DoneArg *a = new DoneArg{s, r, status};
+    done_cb(a);
+}
+
+// Admission of one request on the set-up stream; returns false (and finishes
+// the request) on failure.
+bool admit(Server *s, const std::shared_ptr<Request> &r) {
+    rsf_ctx *c = s->ctx;
+    const rsf_request &q = r->req;
+    ++s->admitted;
+    if (s->inject_admission > 0 && (int64_t)s->admitted == s->inject_admission) {
+        rsf::set_last_error("injected set-up failure");
+        finish_now(s, r, RSF_E_CUDA);
+        return false;
+    }
+    const bool stage_img = !on_device(q.volume);
+    r->bytes = footprint(q, stage_img);
+    {
+        std::lock_guard<std::mutex> lk(c->alloc_mu);
+        c->used += r->bytes;
+    }
+    auto fail_admit = [&](int st) {
+        if (r->mem) cudaFreeAsync(r->mem, s->s_setup);
+        r->mem = nullptr;
+        std::lock_guard<std::mutex> lk(c->alloc_mu);
+        c->used -= std::min<uint64_t>(c->used, r->bytes);
+        finish_now(s, r, st);
+        return false;
+    };
+    if (q.stream) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return fail_admit(RSF_E_CUDA);
+        cudaEventRecord(ev, (cudaStream_t)q.stream);
+        cudaStreamWaitEvent(s->s_setup, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    if (cudaMallocAsync(&r->mem, r->bytes, s->s_setup) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_admit(RSF_E_NOMEM);
+    }
+    const long long n = (long long)q.nx * q.ny * q.nz;
+    const int px = rsf::tiled_pitch((int)q.nx);
+    r->n = n;
+    r->taps = make_taps(q.sigma);
+    r->imgtype = (int)q.vt;
+    r->storage = (int)q.storage;
+    char *p = static_cast<char *>(r->mem);
+    auto take = [&](size_t b) {
+        char *x = p;
+        p += align256(b);
+        return x;
+    };
+    rsf::BrickDev &d = r->d;
+    d = rsf::BrickDev{};
+    d.nx = (int)q.nx;
+    d.ny = (int)q.ny;
+    d.nz = (int)q.nz;
+    d.px = px;
+    for (int k = 0; k < 2; ++k) d.phi[k] = reinterpret_cast<float *>(take(sizeof(float) * n));
+    for (int k = 0; k < 2; ++k) d.q[k] = reinterpret_cast<float *>(take(sizeof(float) * n));
+    float *prof = reinterpret_cast<float *>(take(sizeof(float) * (q.nx + q.ny + q.nz)));
+    float *cs = reinterpret_cast<float *>(take(64));
+    d.prof = prof;
+    d.cs = cs;
+    const long long np = (long long)px * q.ny * q.nz;
+    rsf::tiled_stage_views(r->storage, take(rsf::tiled_stage_bytes(r->storage, np)), np, &d.u4, &d.ab, &d.abxy);
+    if (stage_img) {
+        void *img = take(dtype_size(q.vt) * n);
+        if (cudaMemcpyAsync(img, q.volume, dtype_size(q.vt) * n, cudaMemcpyDefault, s->s_setup) != cudaSuccess)
+            return fail_admit(RSF_E_CUDA);
+        d.img = img;
+    } else {
+        d.img = q.volume;
+    }
+    d.eps = q.eps;
+    d.lambda1 = q.lambda1;
+    d.lambda2 = q.lambda2;
+    d.nu = q.nu;
+    d.mu = q.mu;
+    d.dt = q.dt;
+    d.zc = 16;
+    d.flip = (int)(s->tick & 1);  // its iteration k runs at tick (admission tick + k)
+    // centring constants (the profiles are set below, exactly as rsf_evolve computes them)
+    rsf::Fields f;
+    f.d = rsf::Dims{d.nx, d.ny, d.nz, (long long)q.nx * q.ny, n};
+    f.partials = s->partials;
+    f.cs = cs;
+    if (rsf::image_stats(d.img, (int)q.vt, f, s->s_setup) != cudaSuccess) return fail_admit(RSF_E_CUDA);
+    std::vector<float> pr((size_t)(q.nx + q.ny + q.nz));
+    rsf::zero_padding_profiles(r->taps, d.nx, d.ny, d.nz, pr.data());
+    for (size_t o = 0; o < pr.size(); o += kParamChunk) {
+        ParamChunk ch;
+        ch.offset = (int)o;
+        ch.count = (int)std::min<size_t>(kParamChunk, pr.size() - o);
+        memcpy(ch.v, pr.data() + o, sizeof(float) * ch.count);
+        k_put<<<(ch.count + 255) / 256, 256, 0, s->s_setup>>>(ch, prof);
+    }
+    if (cudaMemcpyAsync(d.phi[0], q.phi0, sizeof(float) * n, cudaMemcpyDefault, s->s_setup) != cudaSuccess)
+        return fail_admit(RSF_E_CUDA);
+    if (q.iters > 0 && rsf::tiled_q_init(d.phi[0], d.q[0], n, q.eps, s->s_setup) != cudaSuccess)
+        return fail_admit(RSF_E_CUDA);
+    if (rsf::tiled_prepare(r->storage, r->taps.R) != cudaSuccess) return fail_admit(RSF_E_CUDA);
+    if (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess) return fail_admit(RSF_E_CUDA);
+    cudaEventRecord(r->ready, s->s_setup);
+    if (cudaGetLastError() != cudaSuccess) return fail_admit(RSF_E_CUDA);
+    return true;
+}
+
+// Retire an active request after its last launch: copy out (unless cancelled),
+// stamp completion, return its memory in stream order.
+void retire(Server *s, const std::shared_ptr<Request> &r, bool cancelled) {
+    rsf_ctx *c = s->ctx;
+    int st = RSF_OK;
+    if (cancelled) {
+        st = RSF_E_CANCELLED;
+    } else if (cudaMemcpyAsync(r->req.phi_out, r->d.phi[r->req.iters & 1], sizeof(float) * r->n, cudaMemcpyDefault,
+                               s->s_comp) != cudaSuccess) {
+        st = RSF_E_CUDA;
+    }
+    cudaLaunchHostFunc(s->s_comp, done_cb, new DoneArg{s, r, st});
+    cudaFreeAsync(r->mem, s->s_comp);
+    if (r->ready) cudaEventDestroy(r->ready);
+    r->mem = nullptr;
+    std::lock_guard<std::mutex> lk(c->alloc_mu);
+    c->used -= std::min<uint64_t>(c->used, r->bytes);
+}
+
+void rebuild_groups(Server *s) {
+    std::vector<std::shared_ptr<Request>> order = s->active;
+    std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a->n > b->n; });
+    std::vector<GroupSpec> specs;
+    std::vector<std::tuple<int, int, int>> keys;
+    for (const auto &r : order) {
+        std::tuple<int, int, int> k{r->taps.R, r->imgtype, r->storage};
+        size_t gi = std::find(keys.begin(), keys.end(), k) - keys.begin();
+        if (gi == keys.size()) {
+            keys.push_back(k);
+            specs.emplace_back();
+            specs.back().storage = r->storage;
+            specs.back().imgtype = r->imgtype;
+            specs.back().taps = r->taps;
+        }
+        specs[gi].bricks.push_back(r->d);
+    }
+    for (GroupSpec &g : specs) {
+        long long work = 0;
+        int maxnz = 16;
+        for (const rsf::BrickDev &b : g.bricks) {
+            work += (long long)((b.nx + 31) / 32) * ((b.ny + 7) / 8) * b.nz;
+            maxnz = std::max(maxnz, b.nz);
+        }
+        const int zc = (int)std::min<long long>(maxnz, std::max<long long>(16, work / std::max(1LL, 16LL * s->sms)));
+        for (rsf::BrickDev &b : g.bricks) b.zc = zc;
+    }
+    // the copy comes from pageable memory and waits for the compute stream; the
+    // loop already bounds how far it runs ahead, so this costs one short sync
+    s->groups.clear();
+    upload_groups(s->ctx, s->desc, s->s_comp, specs, &s->groups);
+    s->groups_dirty = false;
+}
+
+void loop(Server *s) {
+    rsf_ctx *c = s->ctx;
+    cudaSetDevice(c->device);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> admit_now;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || !s->active.empty(); });
+            if (s->stop) break;
+            // FIFO admission by footprint
+            while (!s->queue.empty()) {
+                std::shared_ptr<Request> r = s->queue.front();
+                if (r->cancel.load()) {
+                    s->queue.pop_front();
+                    lk.unlock();
+                    finish_now(s, r, RSF_E_CANCELLED);
+                    lk.lock();
+                    continue;
+                }
+                const size_t need = footprint(r->req, !on_device(r->req.volume));
+                uint64_t used, budget;
+                {
+                    std::lock_guard<std::mutex> al(c->alloc_mu);
+                    used = c->used;
+                    budget = c->budget;
+                }
+                if (used + need > budget && !s->active.empty()) break;  // wait for retirements
+                s->queue.pop_front();
+                admit_now.push_back(r);
+                if (used + need > budget) break;  // nothing active: admit it alone and try
+            }
+        }
+        for (auto &r : admit_now) {
+            if (admit(s, r)) {
+                cudaStreamWaitEvent(s->s_comp, r->ready, 0);
+                r->done_iters = 0;
+                if (r->req.iters == 0) {
+                    retire(s, r, false);
+                } else {
+                    s->active.push_back(r);
+                    s->groups_dirty = true;
+                }
+            }
+        }
+        if (s->active.empty()) continue;
+        if (s->groups_dirty) rebuild_groups(s);
+        for (const rsf::TiledGroup &g : s->groups) rsf::tiled_iterate(g, (int)(s->tick & 1), nullptr, s->s_comp);
+        ++s->tick;
+        // retire finished or cancelled bricks
+        std::vector<std::shared_ptr<Request>> keep;
+        keep.reserve(s->active.size());
+        for (auto &r : s->active) {
+            ++r->done_iters;
+            const bool cancelled = r->cancel.load();
+            if (cancelled || r->done_iters >= r->req.iters) {
+                retire(s, r, cancelled);
+                s->groups_dirty = true;
+            } else {
+                keep.push_back(r);
+            }
+        }
+        s->active.swap(keep);
+        // bound the run-ahead
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(ev, s->s_comp);
+            s->inflight.push_back(ev);
+        }
+        while ((int)s->inflight.size() > kMaxAhead) {
+            cudaEventSynchronize(s->inflight.front());
+            cudaEventDestroy(s->inflight.front());
+            s->inflight.pop_front();
+        }
+    }
+    // shutdown: cancel what is queued or active, let the GPU finish
+    std::vector<std::shared_ptr<Request>> rest;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        rest.assign(s->queue.begin(), s->queue.end());
+        s->queue.clear();
+    }
+    for (auto &r : rest) finish_now(s, r, RSF_E_CANCELLED);
+    for (auto &r : s->active) retire(s, r, true);
+    s->active.clear();
+    cudaStreamSynchronize(s->s_comp);
+    cudaStreamSynchronize(s->s_setup);
+    for (cudaEvent_t e : s->inflight) cudaEventDestroy(e);
+    s->inflight.clear();
+}
+
+Server *server(rsf_ctx *c, rsf_status *st) {
+    std::lock_guard<std::mutex> lk(c->serve_mu);
+    if (c->server) return static_cast<Server *>(c->server);
+    Server *s = new Server();
+    s->ctx = c;
+    cudaSetDevice(c->device);
+    cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->s_setup, cudaStreamNonBlocking) != cudaSuccess) {
+        *st = cuda_fail(cudaGetLastError(), "serving streams");
+        delete s;
+        return nullptr;
+    }
+    if ((*st = dev_alloc(c, (void **)&s->partials, sizeof(float) * 3 * rsf::kStatBlocks))) {
+        delete s;
+        return nullptr;
+    }
+    s->inject_admission = c->opt_inject_admission;
+    s->th = std::thread(loop, s);
+    c->server = s;
+    return s;
+}
+
+}  // namespace
+
+void rsf_serve_shutdown(rsf_ctx *c) {
+    Server *s = static_cast<Server *>(c->server);
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    if (s->th.joinable()) s->th.join();
+    dev_free(c, s->partials, sizeof(float) * 3 * rsf::kStatBlocks);
+    free_desc(c, s->desc);
+    cudaStreamDestroy(s->s_comp);
+    cudaStreamDestroy(s->s_setup);
+    delete s;
+    c->server = nullptr;
+}
+
+extern "C" rsf_status rsf_submit(rsf_ctx *c, const rsf_request *req, uint64_t *ticket) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    if (!req || !ticket) return fail(RSF_E_INVAL, "null request or ticket pointer");
+    rsf_status st = check_args(req->volume, req->vt, req->nx, req->ny, req->nz, req->phi0, req->phi_out, req->sigma,
+                               req->eps, req->dt, req->iters);
+    if (st) return st;
+    if (req->storage != RSF_STORE_F32 && req->storage != RSF_STORE_BF16 && req->storage != RSF_STORE_F16)
+        return fail(RSF_E_INVAL, "unknown storage %d", (int)req->storage);
+    const int R = make_taps(req->sigma).R;
+    if (!rsf::tiled_supports(R)) return fail(RSF_E_INVAL, "no served kernels for radius %d", R);
+    if (req->halo >= 0 && (2 * (int64_t)req->halo >= req->nx || 2 * (int64_t)req->halo >= req->ny ||
+                           2 * (int64_t)req->halo >= req->nz))
+        return fail(RSF_E_INVAL, "halo %d leaves no core in a %lld x %lld x %lld brick", (int)req->halo,
+                    (long long)req->nx, (long long)req->ny, (long long)req->nz);
+    const size_t need = footprint(*req, !on_device(req->volume));
+    if (need > c->budget)
+        return fail(RSF_E_NOMEM, "request needs %zu bytes of device memory; the budget is %llu", need,
+                    (unsigned long long)c->budget);
+    Server *s = server(c, &st);
+    if (!s) return st;
+    auto r = std::make_shared<Request>();
+    r->req = *req;
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->queue.size() >= kMaxQueue) return fail(RSF_E_BUSY, "request queue full");
+        r->ticket = s->next_ticket++;
+        s->tickets[r->ticket] = r;
+        s->queue.push_back(r);
+        ++s->submitted;
+        if (s->t_first == 0.0) s->t_first = r->t_submit;
+        *ticket = r->ticket;
+    }
+    s->cv.notify_all();
+    return RSF_OK;
+}
+
+extern "C" rsf_status rsf_poll(rsf_ctx *c, uint64_t ticket, double *latency_s) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    Server *s = static_cast<Server *>(c->server);
+    if (!s) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    const int st = it->second->status.load();
+    if (st == RSF_PENDING) return RSF_PENDING;
+    if (latency_s) *latency_s = it->second->t_done - it->second->t_submit;
+    s->tickets.erase(it);
+    if (st < 0) return fail(st, "request %llu ended with status %d", (unsigned long long)ticket, st);
+    return st;
+}
+
+extern "C" rsf_status rsf_wait(rsf_ctx *c, uint64_t ticket, int32_t timeout_ms) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    Server *s = static_cast<Server *>(c->server);
+    if (!s) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->tickets.find(ticket);
+        if (it == s->tickets.end()) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+        std::shared_ptr<Request> r = it->second;
+        auto done = [&] { return r->status.load() != RSF_PENDING; };
+        if (timeout_ms < 0) {
+            s->done_cv.wait(lk, done);
+        } else if (!s->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+            return fail(RSF_E_TIMEOUT, "request %llu still pending after %d ms", (unsigned long long)ticket,
+                        (int)timeout_ms);
+        }
+    }
+    return rsf_poll(c, ticket, nullptr);
+}
+
+extern "C" rsf_status rsf_cancel(rsf_ctx *c, uint64_t ticket) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    Server *s = static_cast<Server *>(c->server);
+    if (!s) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    it->second->cancel.store(true);
+    s->cv.notify_all();
+    return RSF_OK;
+}
+
+extern "C" rsf_status rsf_serve_stats(rsf_ctx *c, rsf_serve_stat *out) {
+    if (!c || !out) return fail(RSF_E_INVAL, "null context or output");
+    memset(out, 0, sizeof *out);
+    Server *s = static_cast<Server *>(c->server);
+    if (!s) return RSF_OK;
+    std::lock_guard<std::mutex> lk(s->mu);
+    out->submitted = s->submitted;
+    out->completed = s->completed;
+    out->failed = s->failed;
+    out->cancelled = s->cancelled;
+    out->queued = s->queue.size();
+    out->voxel_iterations = s->vox_iters;
+    out->busy_s = s->t_last > s->t_first ? s->t_last - s->t_first : 0.0;
+    if (!s->latencies.empty()) {
+        std::vector<double> l = s->latencies;
+        std::sort(l.begin(), l.end());
+        auto pct = [&](double q) {
+            const size_t i = (size_t)std::min<double>((double)l.size() - 1, std::ceil(q * l.size()) - 1);
+            return l[i];
+        };
+        out->latency_p50_s = pct(0.50);
+        out->latency_p99_s = pct(0.99);
+        out->latency_max_s = l.back();
+    }
+    return RSF_OK;
+}

@@ -122,7 +122,7 @@ struct GroupArgs {
     const BrickDev *bricks;
     const int *starts;  // nb + 1 CTA offsets of this kernel within the launch
     int nb;
-    int parity;         // iteration parity: reads phi[parity], q[parity], writes the other
+    int parity;         // launch parity: a brick reads phi[p], q[p] with p = parity ^ flip, writes the other
 };
 
 // ---------------------------------------------------------------- x / y
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 2>()) k_ta_xy(Gro
     const BrickDev &B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
-    ProHP<ImgT> pro{G.parity ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
+    ProHP<ImgT> pro{(G.parity ^ B.flip) ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
     OutU4<S> out{reinterpret_cast<typename Store<S>::V4 *>(B.u4), B.px, (long long)B.px * B.ny};
     xy_tile<R, 2>(pro, out, B.nx, B.ny, B.nz, B.nx, tl.x0, tl.y0, tl.za, t, sm);
 }
@@ -460,7 +460,8 @@ __global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_tb_z(GroupArgs G,
     const long long col = (long long)min(y, ny - 1) * nx + min(x, nx - 1);
     const int px = B.px;
     const long long pplane = (long long)px * ny;
-    const float *phi = G.parity ? B.phi[1] : B.phi[0];
+    const int par = G.parity ^ B.flip;
+    const float *phi = par ? B.phi[1] : B.phi[0];
 
     int poff[NPE], noff[NNE];
 #pragma unroll
@@ -529,8 +530,8 @@ __global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_tb_z(GroupArgs G,
     const float mu = B.mu, nu = B.nu, dt = B.dt;
     const ImgT *img = reinterpret_cast<const ImgT *>(B.img);
     long long qz = (long long)z0 * plane + col;  // this thread's voxel index at the output plane
-    float *phi_out = G.parity ? B.phi[0] : B.phi[1];
-    float *q_out = G.parity ? B.q[0] : B.q[1];
+    float *phi_out = par ? B.phi[0] : B.phi[1];
+    float *q_out = par ? B.q[0] : B.q[1];
 
     const float2 *src = B.abxy + (long long)min(y, ny - 1) * px + min(x, nx - 1);
     auto load = [&](int s) -> float2 {

@@ -26,9 +26,10 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
-            "rsf_set_option", "rsf_evolve_batch")
+            "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
+            "rsf_serve_stats")
 
-OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH = 1, 2, 3, 4, 5
+OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION = 1, 2, 3, 4, 5, 6
 PATHS = {"auto": 0, "passes": 1, "tiled": 2}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 
@@ -42,6 +43,19 @@ class Brick(ctypes.Structure):
                 ("sigma", ctypes.c_float), ("eps", ctypes.c_float), ("lambda1", ctypes.c_float),
                 ("lambda2", ctypes.c_float), ("nu", ctypes.c_float), ("mu", ctypes.c_float), ("dt", ctypes.c_float),
                 ("iters", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    """rsf_request (include/rsf.h)."""
+    _fields_ = Brick._fields_ + [("storage", ctypes.c_int32), ("halo", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class ServeStat(ctypes.Structure):
+    """rsf_serve_stat (include/rsf.h)."""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("voxel_iterations", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("latency_p50_s", ctypes.c_double), ("latency_p99_s", ctypes.c_double),
+                ("latency_max_s", ctypes.c_double)]
 
 
 class RSFError(RuntimeError):
@@ -84,6 +98,16 @@ def load_library(path: str = LIB_PATH):
     L.rsf_evolve_noalloc.restype = i32
     L.rsf_evolve_batch.argtypes = [vp, ctypes.POINTER(Brick), i32]
     L.rsf_evolve_batch.restype = i32
+    L.rsf_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    L.rsf_submit.restype = i32
+    L.rsf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
+    L.rsf_poll.restype = i32
+    L.rsf_wait.argtypes = [vp, ctypes.c_uint64, i32]
+    L.rsf_wait.restype = i32
+    L.rsf_cancel.argtypes = [vp, ctypes.c_uint64]
+    L.rsf_cancel.restype = i32
+    L.rsf_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStat)]
+    L.rsf_serve_stats.restype = i32
     L.rsf_set_option.argtypes = [vp, i32, i64]
     L.rsf_set_option.restype = i32
     L.rsf_last_error.argtypes = []
@@ -243,6 +267,38 @@ class Context:
         _order_after_caller(*[x for pair in keep for x in pair], *outs)
         _check(load_library().rsf_evolve_batch(self._h, arr, len(items)))
         return outs
+
+    # serving -----------------------------------------------------------------
+    def submit(self, volume, phi0, params, iters: int, out, storage: str = "f32", halo: int = -1, stream=None):
+        """rsf_submit; returns the ticket.  `volume`, `phi0`, `out` stay owned by
+        the caller and must stay valid until the ticket is no longer pending."""
+        p = Params.of(params)
+        nz, ny, nx = _shape(volume)
+        if _shape(phi0) != (nz, ny, nx) or _shape(out) != (nz, ny, nx):
+            raise ValueError("volume, phi0 and out shapes differ")
+        _order_after_caller(volume, phi0, out)
+        r = Request(_ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0), _ptr(out), *p.tuple(), int(iters),
+                    STORAGE[storage], int(halo), int(stream.cuda_stream) if stream is not None else 0)
+        t = ctypes.c_uint64()
+        _check(load_library().rsf_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        """(status, latency_s): status RSF_PENDING (1) or RSF_OK (0); errors raise."""
+        lat = ctypes.c_double(-1.0)
+        st = _check(load_library().rsf_poll(self._h, int(ticket), ctypes.byref(lat)))
+        return st, lat.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        return _check(load_library().rsf_wait(self._h, int(ticket), int(timeout_ms)))
+
+    def cancel(self, ticket: int):
+        _check(load_library().rsf_cancel(self._h, int(ticket)))
+
+    def serve_stats(self) -> dict:
+        st = ServeStat()
+        _check(load_library().rsf_serve_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServeStat._fields_}
 
     def set_storage(self, name: str):
         """Storage of the intermediate fields: 'f32', 'bf16' or 'f16'."""

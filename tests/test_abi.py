@@ -69,3 +69,13 @@ def test_prof_names(lib):
 
 def test_set_option_rejects_bad_keys_without_a_context(lib):
     assert lib.rsf_set_option(None, 1, 0) == -1
+
+
+def test_serving_entry_points_validate_without_a_gpu(lib):
+    import ctypes as C
+    t = C.c_uint64()
+    assert lib.rsf_submit(None, None, C.byref(t)) == -1
+    assert lib.rsf_poll(None, 1, None) == -1
+    assert lib.rsf_wait(None, 1, 0) == -1
+    assert lib.rsf_cancel(None, 1) == -1
+    assert lib.rsf_evolve_batch(None, None, 0) == -1
