@@ -71,6 +71,23 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest of each rank's `x` (the slowest rank's time); `x` itself at N = 1."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds_max: float) -> float:
+    """Whole-job throughput in G units/s: every rank processes `units_per_rank`
+    (weak scaling), divided by the slowest rank's time."""
+    return units_per_rank * world / seconds_max / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling while the timed region runs."""
 
@@ -223,12 +240,8 @@ def run_batch(args, rank, world, local):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = padded * iters * args.steps * world / (ms_max / 1e3) / 1e9
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), world)
+    value = whole_job_rate(padded * iters * args.steps, world, ms_max / 1e3)
     # per-kernel device time: one more step with per-launch events (direct launches)
     ctx.prof_enable(True)
     ctx.evolve_batch(items)
@@ -247,10 +260,8 @@ def run_batch(args, rank, world, local):
         for _ in range(args.steps):
             ctx.evolve_batch(hitems)
         torch.cuda.synchronize()
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": padded * iters * args.steps * world / float(te.item()) / 1e9, "unit": "GVoxel-iterations/s",
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": whole_job_rate(padded * iters * args.steps, world, te), "unit": "GVoxel-iterations/s",
                "h2d_bytes_per_step": int(sum(v.nbytes + p.nbytes for v, p in bricks)),
                "d2h_bytes_per_step": int(sum(p.nbytes for _, p in bricks))}
     if rank == 0:
@@ -270,7 +281,7 @@ def run_batch(args, rank, world, local):
                                    f"halo 12) from a 2048x2048x1024 field, sigma=4 (17 taps), {iters} iterations, "
                                    "one batched launch per kernel per iteration, CUDA graph between retirements",
                        "bricks": nb, "padded_voxels": int(padded), "core_voxels": int(core),
-                       "core_value": core * iters * args.steps * world / (ms_max / 1e3) / 1e9,
+                       "core_value": whole_job_rate(core * iters * args.steps, world, ms_max / 1e3),
                        "storage": args.storage, "l2": "inputs larger than L2",
                        "parallelism": f"replicas{world}" if world > 1 else "single-gpu"},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -288,6 +299,97 @@ def run_batch(args, rank, world, local):
     ctx.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def _serve_worker(job):
+    from paper_2404_02813_gb300 import synth
+    k, spec = job
+    vol = synth.serve_request_volume(spec, k)
+    return vol, synth.mean_rule_phi0(vol)
+
+
+def serve_params(spec):
+    P = {"lightsheet": P_LIGHTSHEET, "microct": P_MICROCT, "milling": 255.0}[spec.source]
+    return dict(sigma=spec.sigma, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P * P, mu=1.0, dt=0.1)
+
+
+def run_serve(args, rank, world, local):
+    """Poisson arrivals of brick requests at several rates through rsf_submit (FP16
+    storage, 150 GB budget), against sequential plain FP32 solves of the same requests
+    (FIFO single-server latencies from their measured service times)."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+    from paper_2404_02813_gb300 import synth
+    npool = 32
+    specs = synth.serve_request_specs(npool)
+    with ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)), mp_context=get_context("spawn")) as ex:
+        pool = list(ex.map(_serve_worker, list(enumerate(specs)), chunksize=1))
+    import torch
+    from paper_2404_02813_gb300 import rsf
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    dev = [(torch.from_numpy(v).cuda(), torch.from_numpy(p).cuda()) for v, p in pool]
+    rng = np.random.default_rng(5005)
+    rates = [float(r) for r in args.rates.split(",")]
+    nreq = args.requests
+    # the request list: pool volume, and a fresh iteration count per request
+    reqs = [(int(rng.integers(0, npool)), int(rng.integers(50, 501))) for _ in range(nreq)]
+    work = [dev[k][0].numel() * it for k, it in reqs]
+    # sequential plain FP32 service times: one timed solve per pool volume, linear in iterations
+    seq = rsf.Context(local)
+    per_it, fixed = [], []
+    for k, (v, ph) in enumerate(dev):
+        prm = serve_params(specs[k])
+        seq.evolve(v, ph, prm, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter(); seq.evolve(v, ph, prm, 10); t10 = time.perf_counter() - t0
+        t0 = time.perf_counter(); seq.evolve(v, ph, prm, 60); t60 = time.perf_counter() - t0
+        per_it.append(max((t60 - t10) / 50.0, 1e-7))
+        fixed.append(max(t10 - 10 * per_it[-1], 0.0))
+    seq.close()
+    service = [fixed[k] + per_it[k] * it for k, it in reqs]
+    results = []
+    for rate in rates:
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+        ctx = rsf.Context(local, hbm_budget_bytes=int(150e9))
+        outs = []
+        t0 = time.perf_counter()
+        tickets = []
+        for i, (k, it) in enumerate(reqs):
+            dt_ = t0 + arrivals[i] - time.perf_counter()
+            if dt_ > 0:
+                time.sleep(dt_)
+            v, ph = dev[k]
+            o = torch.empty_like(ph)
+            outs.append(o)
+            tickets.append(ctx.submit(v, ph, serve_params(specs[k]), it, o, storage="f16"))
+        for t in tickets:
+            ctx.wait(t, -1)
+        wall = time.perf_counter() - t0
+        st = ctx.serve_stats()
+        ctx.close()
+        # sequential FIFO server with the measured service times
+        fin, lat = 0.0, []
+        for a, sv in zip(arrivals, service):
+            fin = max(fin, a) + sv
+            lat.append(fin - a)
+        lat = np.array(lat)
+        results.append({
+            "offered_req_s": rate, "achieved_req_s": nreq / wall,
+            "gvox_it_s": st["voxel_iterations"] / max(st["busy_s"], 1e-9) / 1e9,
+            "p50_s": st["latency_p50_s"], "p99_s": st["latency_p99_s"],
+            "sequential_fp32": {"gvox_it_s": sum(work) / sum(service) / 1e9,
+                                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))}})
+    best = max(r["gvox_it_s"] for r in results)
+    line = {"metric": "GVoxel-iterations/s", "value": best, "unit": "GVoxel-iterations/s", "n_gpus": 1,
+            "steps": len(rates), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 compute, f16 storage", "data": "synthetic (light-sheet, micro-CT and milling-like bricks)",
+            "config": {"workload": f"serve: {nreq} brick requests per rate, Poisson arrivals, core edges log-uniform "
+                                   "32-256 + 3 sigma halo, sigma in {2,3,4,6}, iterations U{50..500}, FP16 storage, "
+                                   "150 GB budget, 64 slots; request images drawn from a pool of 32",
+                       "rates": results}}
+    print(json.dumps(line), flush=True)
 
 
 def workload_desc(name, vol, params, iters):
@@ -357,7 +459,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsf", choices=["rsf", "reference"])
     ap.add_argument("--workload", default="lightsheet512",
-                    choices=["lightsheet512", "lightsheet512_s5", "tree64", "bricks256"])
+                    choices=["lightsheet512", "lightsheet512_s5", "tree64", "bricks256", "serve"])
+    ap.add_argument("--requests", type=int, default=200, help="requests per arrival rate (serve)")
+    ap.add_argument("--rates", default="8,16,24,32", help="Poisson arrival rates in requests/s (serve)")
     ap.add_argument("--bricks", type=int, default=None, help="number of bricks of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -377,6 +481,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "bricks256":
         return run_batch(args, rank, world, local)
+    if args.workload == "serve":
+        return run_serve(args, rank, world, local)
 
     import torch
     import torch.distributed as dist
@@ -422,12 +528,9 @@ def main():
     prof = ctx.prof_get()
     ctx.prof_enable(False)
 
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    total_vox_it = n_vox * iters * args.steps * world
-    value = total_vox_it / (ms_max / 1e3) / 1e9
+    ms_max = max_over_ranks(ms, world)
+    rank_vox_it = n_vox * iters * args.steps
+    value = whole_job_rate(rank_vox_it, world, ms_max / 1e3)
 
     # end to end through the same call with pinned host buffers
     e2e = None
@@ -442,10 +545,8 @@ def main():
         for _ in range(args.steps):
             ctx.evolve(vh, ph, params, iters, out=oh)
         torch.cuda.synchronize()
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": total_vox_it / float(te.item()) / 1e9, "unit": "GVoxel-iterations/s",
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": whole_job_rate(rank_vox_it, world, te), "unit": "GVoxel-iterations/s",
                "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + ph.numel() * 4),
                "d2h_bytes_per_step": int(oh.numel() * 4)}
 

@@ -173,6 +173,9 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   (default): a size heuristic.
  *   RSF_OPT_GRAPH   1 (default): rsf_evolve_batch replays its iterations from
  *                   a captured CUDA graph; 0: direct launches.
+ *   RSF_OPT_SERVE_SLOTS  the most bricks the serving loop advances together
+ *                   (default 64); further requests wait in the queue.  Read
+ *                   when the serving loop starts (the first rsf_submit).
  *   RSF_OPT_FAULT_ADMISSION  k > 0: the serving loop fails the set-up of its
  *                   k-th admission with RSF_E_CUDA, on the host, without any
  *                   device work (for testing failure handling); 0: off.  Read
@@ -186,6 +189,7 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 #define RSF_OPT_AUTOTUNE 4
 #define RSF_OPT_GRAPH 5
 #define RSF_OPT_FAULT_ADMISSION 6
+#define RSF_OPT_SERVE_SLOTS 7
 #define RSF_PATH_AUTO 0
 #define RSF_PATH_PASSES 1
 #define RSF_PATH_TILED 2

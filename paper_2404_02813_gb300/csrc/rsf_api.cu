@@ -499,6 +499,10 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
                 return fail(RSF_E_INVAL, "unknown storage %lld", (long long)value);
             c->opt_storage = (int)value;
             return RSF_OK;
+        case RSF_OPT_SERVE_SLOTS:
+            if (value < 1 || value > (1 << 20)) return fail(RSF_E_INVAL, "slots must lie in [1, 2^20]");
+            c->opt_serve_slots = value;
+            return RSF_OK;
         case RSF_OPT_FAULT_ADMISSION:
             if (value < 0) return fail(RSF_E_INVAL, "fault admission index must be >= 0");
             c->opt_inject_admission = value;

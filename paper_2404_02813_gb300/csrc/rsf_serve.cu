@@ -107,6 +107,7 @@ struct Server {
     std::vector<double> latencies;
     // host-side fault injection: the k-th admission (1-based) fails its set-up
     int64_t inject_admission = 0;
+    int64_t slots = 64;  // bricks advanced together at most
 };
 
 void CUDART_CB done_cb(void *p) {
@@ -332,6 +333,7 @@ void loop(Server *s) {
                     budget = c->budget;
                 }
                 if (used + need > budget && !s->active.empty()) break;  // wait for retirements
+                if ((int64_t)(s->active.size() + admit_now.size()) >= s->slots) break;  // wait for a free slot
                 s->queue.pop_front();
                 admit_now.push_back(r);
                 if (used + need > budget) break;  // nothing active: admit it alone and try
@@ -413,6 +415,7 @@ Server *server(rsf_ctx *c, rsf_status *st) {
         return nullptr;
     }
     s->inject_admission = c->opt_inject_admission;
+    s->slots = c->opt_serve_slots;
     s->th = std::thread(loop, s);
     c->server = s;
     return s;

@@ -249,3 +249,64 @@ def brick_specs(n_bricks: int = 256, core_range=(64, 192), halo: int = 12,
         org = tuple(int(rng.integers(halo, e - c - halo)) for e, c in zip(extent_xyz, core))
         out.append(BrickSpec(org, core, halo))
     return out
+
+
+def milling_volume_u8(shape_zyx, workload: int = 4, brick: int = 0, vessel_fraction: float = 0.04,
+                      r_range=(1.0, 2.0), fg: float = 200.0, bg: float = 30.0, stripe: float = 0.2,
+                      stripe_period: float = 64.0, noise: float = 20.0, psf: float = 1.0) -> np.ndarray:
+    """uint8 milling-microscopy-like volume: a dense capillary bed (radius 1-2 voxels,
+    about 4 % vessel fraction), illumination striped by +-20 % along z (period 64
+    voxels, a reading: the period is not given), Gaussian noise std 20."""
+    rng = rng_for(workload, brick)
+    nz, ny, nx = shape_zyx
+    mean_len, mean_r = 13.0, 0.5 * (r_range[0] + r_range[1])
+    n_seg = max(4, int(vessel_fraction * nx * ny * nz / (np.pi * mean_r ** 2 * mean_len)))
+    seg = vessel_segments(rng, (nx, ny, nz), n_seg, r_range)
+    occ = _blur(rasterize(seg, (0, 0, 0), shape_zyx), (psf, psf, psf))
+    z = np.arange(nz, dtype=np.float32)[:, None, None]
+    gain = 1.0 + stripe * np.sin(2.0 * np.pi * z / stripe_period)
+    img = (bg + (fg - bg) * occ) * gain + rng.normal(0.0, noise, size=occ.shape)
+    return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+
+
+@dataclass
+class ServeRequestSpec:
+    source: str          # "lightsheet", "microct" or "milling"
+    core_zyx: Tuple[int, int, int]
+    sigma: float
+    iters: int
+
+    @property
+    def halo(self) -> int:
+        return int(round(3 * self.sigma))
+
+    @property
+    def padded_zyx(self) -> Tuple[int, int, int]:
+        return tuple(c + 2 * self.halo for c in self.core_zyx)
+
+
+def serve_request_specs(n: int, workload: int = 5, core_range=(32, 256), sigmas=(2.0, 3.0, 4.0, 6.0),
+                        iters_range=(50, 500)):
+    """Request mix: core edges log-uniform in core_range per axis, sigma uniform in
+    `sigmas`, iterations uniform in iters_range, data source uniform over the three."""
+    rng = rng_for(workload, 0)
+    lo, hi = np.log(core_range[0]), np.log(core_range[1])
+    out = []
+    for _ in range(n):
+        core = tuple(int(round(np.exp(rng.uniform(lo, hi)))) for _ in range(3))
+        out.append(ServeRequestSpec(str(rng.choice(["lightsheet", "microct", "milling"])), core,
+                                    float(rng.choice(sigmas)), int(rng.integers(iters_range[0], iters_range[1] + 1))))
+    return out
+
+
+def serve_request_volume(spec: ServeRequestSpec, k: int) -> np.ndarray:
+    """The halo-padded image of one request, from the generator of its source."""
+    shp = spec.padded_zyx
+    if spec.source == "lightsheet":
+        return lightsheet_volume_u16(shp, workload=5, brick=k)
+    if spec.source == "microct":
+        f = MicroCTField(extent_xyz=(max(shp[2] + 64, 512), max(shp[1] + 64, 512), max(shp[0] + 64, 512)),
+                         workload=500 + k)
+        bs = BrickSpec((spec.halo + 8, spec.halo + 8, spec.halo + 8), tuple(reversed(spec.core_zyx)), spec.halo)
+        return f.brick(bs, k)
+    return milling_volume_u8(shp, workload=5, brick=k)
