@@ -52,6 +52,18 @@ constexpr int kAZO = kAZT / (kAZThreads / 32);
 constexpr int kPFB = 2;           // (a, b) planes loaded ahead in the z march
 
 __device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// The taps of Eq. (7) duplicated into (g_k, g_k) pairs, passed by value: the
+// first operand of a packed f32x2 FMA over a field pair, read from the
+// kernel's parameter space.
+struct TapPairs {
+    float2 g[2 * RMAX + 1];
+};
+inline TapPairs tap_pairs(const Taps &t) {
+    TapPairs p{};
+    for (int k = 0; k <= 2 * t.R; ++k) p.g[k] = make_float2(t.g[k], t.g[k]);
+    return p;
+}
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 // ------------------------------------------------------------- storage
@@ -127,13 +139,20 @@ struct GroupArgs {
 
 // ---------------------------------------------------------------- x / y
 
+// A producer of the x/y kernel's input pairs: plane(off) gives the plane at
+// element offset `off`, fetch(plane, o) the raw values at offset o within it,
+// apply() the NP float2 pairs (zero outside the brick).
 template <class ImgT>
 struct ProHP {  // (H I~, H), ((1-H) I~, 1-H) from q and the centred image
     const float *q;
     const ImgT *img;
     float inv_s, nms;
     struct Raw { float q, im; };
-    __device__ __forceinline__ Raw fetch(long long p) const { return Raw{__ldg(q + p), centred(img, p, inv_s, nms)}; }
+    struct Plane { const float *q; const ImgT *img; };
+    __device__ __forceinline__ Plane plane(long long off) const { return Plane{q + off, img + off}; }
+    __device__ __forceinline__ Raw fetch(const Plane &pl, int o) const {
+        return Raw{__ldg(pl.q + o), fmaf((float)__ldg(pl.img + o), inv_s, nms)};
+    }
     __device__ __forceinline__ Raw zero() const { return Raw{0.f, 0.f}; }
     __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
         if (inside) {
@@ -150,7 +169,9 @@ template <class S>
 struct ProAB {  // (a, b) as stored by rsf_ta_z (pitched)
     const typename Store<S>::V2 *ab;
     using Raw = typename Store<S>::V2;
-    __device__ __forceinline__ Raw fetch(long long p) const { return __ldg(ab + p); }
+    struct Plane { const typename Store<S>::V2 *ab; };
+    __device__ __forceinline__ Plane plane(long long off) const { return Plane{ab + off}; }
+    __device__ __forceinline__ Raw fetch(const Plane &pl, int o) const { return __ldg(pl.ab + o); }
     __device__ __forceinline__ Raw zero() const { return Raw{}; }
     __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
         v[0] = inside ? Store<S>::unpack2(r) : make_float2(0.f, 0.f);
@@ -177,7 +198,7 @@ constexpr int xy_min_blocks() { return R <= 6 ? 3 : 2; }
 // Input row pitch `ipx`; output pitch `opx`; `Out` writes the NP pairs.
 template <int R, int NP, class Pro, class Out>
 __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, int ny, int nz, int ipx, int x0,
-                                        int y0, int za, const Taps &t, float2 *sm) {
+                                        int y0, int za, const TapPairs &t, float2 *sm) {
     using L = XYLayout<R, NP>;
     using Raw = typename Pro::Raw;
     constexpr int T = 2 * R + 1;
@@ -187,16 +208,15 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
     static_assert(NE <= 32, "tile entries per thread exceed the mask");
     float2 *in = sm;
     float2 *xc = sm + L::IN;
-    float2 gg[T];
-#pragma unroll
-    for (int k = 0; k < T; ++k) gg[k] = make_float2(t.g[k], t.g[k]);
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int zb_end = min(za + kXYPlanes, nz);
     const long long iplane = (long long)ipx * ny;
 
+    // tile entry e of this thread: offset within the plane (-1 outside the brick)
+    // and shared-memory index; entries e < NFULL always lie inside the tile
+    constexpr int NFULL = L::H * L::W / kXYThreads;
     int eoff[NE], esm[NE];
-    unsigned inside = 0;
 #pragma unroll
     for (int e = 0; e < NE; ++e) {
         const int i = threadIdx.x + e * kXYThreads;
@@ -204,23 +224,22 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
         const int ly = ii / L::W, lx = ii - ly * L::W;
         const int gx = x0 + lx - R, gy = y0 + ly - R;
         const bool in_vol = i < L::H * L::W && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        eoff[e] = in_vol ? gy * ipx + gx : 0;
+        eoff[e] = in_vol ? gy * ipx + gx : -1;
         esm[e] = i < L::H * L::W ? ly * L::P + lx : -1;
-        inside |= (in_vol ? 1u : 0u) << e;
     }
     Raw raw[NE];
     auto fetch = [&](int z) {
-        const long long zb = (long long)z * iplane;
+        const auto pl = pro.plane((long long)z * iplane);
 #pragma unroll
-        for (int e = 0; e < NE; ++e) raw[e] = ((inside >> e) & 1u) ? pro.fetch(zb + eoff[e]) : pro.zero();
+        for (int e = 0; e < NE; ++e) raw[e] = eoff[e] >= 0 ? pro.fetch(pl, eoff[e]) : pro.zero();
     };
     fetch(za);
     for (int z = za; z < zb_end; ++z) {
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
-            if (esm[e] >= 0) {
+            if (e < NFULL || esm[e] >= 0) {
                 float2 v[NP];
-                pro.apply(raw[e], (inside >> e) & 1u, v);
+                pro.apply(raw[e], eoff[e] >= 0, v);
 #pragma unroll
                 for (int p = 0; p < NP; ++p) in[p * L::H * L::P + esm[e]] = v[p];
             }
@@ -243,7 +262,7 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
                     for (int o = 0; o < XT; ++o) {
                         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int k = 0; k < T; ++k) acc = f2fma(gg[k], w[o + k], acc);
+                        for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
                         xc[(p * L::H + row) * kXYT + xo + o] = acc;
                     }
                 }
@@ -262,37 +281,40 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
                 for (int o = 0; o < YT; ++o) {
                     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int k = 0; k < T; ++k) acc = f2fma(gg[k], w[o + k], acc);
+                    for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
                     res[p][o] = acc;
                 }
             }
             if (gx < nx) {
                 const int gy0 = y0 + warp * YT;
+                const auto op = out.plane(z);
 #pragma unroll
                 for (int o = 0; o < YT; ++o)
-                    if (gy0 + o < ny) out(z, gy0 + o, gx, res[0][o], res[NP - 1][o]);
+                    if (gy0 + o < ny) out(op, (gy0 + o) * out.px + gx, res[0][o], res[NP - 1][o]);
             }
         }
         __syncthreads();  // the next plane reuses the tiles
     }
 }
 
+// Writers of the x/y kernel's outputs: plane(z) gives plane z, operator()
+// stores at offset y * px + x within it.
 template <class S>
 struct OutU4 {  // four H-product fields -> pitched storage
     typename Store<S>::V4 *u;
     int px;
     long long pplane;
-    __device__ __forceinline__ void operator()(int z, int y, int x, float2 a, float2 b) const {
-        u[(long long)z * pplane + (long long)y * px + x] = Store<S>::pack4(make_float4(a.x, a.y, b.x, b.y));
+    __device__ __forceinline__ typename Store<S>::V4 *plane(int z) const { return u + (long long)z * pplane; }
+    __device__ __forceinline__ void operator()(typename Store<S>::V4 *pl, int o, float2 a, float2 b) const {
+        pl[o] = Store<S>::pack4(make_float4(a.x, a.y, b.x, b.y));
     }
 };
 struct OutAB {  // x/y-convolved (a, b), FP32, pitched
     float2 *ab;
     int px;
     long long pplane;
-    __device__ __forceinline__ void operator()(int z, int y, int x, float2 a, float2) const {
-        ab[(long long)z * pplane + (long long)y * px + x] = a;
-    }
+    __device__ __forceinline__ float2 *plane(int z) const { return ab + (long long)z * pplane; }
+    __device__ __forceinline__ void operator()(float2 *pl, int o, float2 a, float2) const { pl[o] = a; }
 };
 
 // CTA -> (brick, tile) for the x/y kernels: tiles (tx, ty, tz) of 32 x 32 x kXYPlanes.
@@ -307,10 +329,10 @@ __device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev 
 }
 
 template <int R, class ImgT, class S>
-__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 2>()) k_ta_xy(GroupArgs G, Taps t) {
+__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 2>()) k_ta_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
-    const BrickDev &B = G.bricks[b];
+    const BrickDev B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
     ProHP<ImgT> pro{(G.parity ^ B.flip) ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
@@ -319,10 +341,10 @@ __global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 2>()) k_ta_xy(Gro
 }
 
 template <int R, class S>
-__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 1>()) k_tb_xy(GroupArgs G, Taps t) {
+__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 1>()) k_tb_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
-    const BrickDev &B = G.bricks[b];
+    const BrickDev B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
     ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
     OutAB out{B.abxy, B.px, (long long)B.px * B.ny};
@@ -331,81 +353,146 @@ __global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 1>()) k_tb_xy(Gro
 
 // ------------------------------------------------------------------ A: z
 
-// x-z slab: 32 columns of one y row, kAZT output planes; every load of the
-// slab in flight at once, then a register-window convolution per lane.  The
-// slab is held as two float2 arrays so that window reads are conflict-free.
-// Consecutive CTAs take consecutive z slabs of one row (shared halos hit L2).
-template <int R>
-constexpr size_t az_smem() { return sizeof(float2) * 2 * (kAZT + 2 * R) * 32; }
+// x-z slabs: 32 columns of one y row and kAZT output planes (plus the R-plane
+// halos).  A persistent CTA walks the slabs of the launch (consecutive slabs
+// are consecutive z ranges of one row, so shared halos hit L2) with a
+// two-stage shared-memory buffer: the cp.async copies of the next slab are in
+// flight while the current one is convolved.  Rows outside the brick are
+// zero-filled by the copy (source size 0).  FP32 storage splits each element's
+// two field pairs into two arrays (conflict-free 8-byte window reads); 16-bit
+// storage keeps the packed element and unpacks the pair it reads.
+template <class S> struct AZSlab;
+template <> struct AZSlab<float> {
+    static constexpr int kArrays = 2;
+};
+template <> struct AZSlab<__half> {
+    static constexpr int kArrays = 1;
+};
+template <> struct AZSlab<__nv_bfloat16> {
+    static constexpr int kArrays = 1;
+};
 
 template <int R, class S>
-__global__ void __launch_bounds__(kAZThreads, R <= 6 ? 4 : (R <= 8 ? 3 : 2)) k_ta_z(GroupArgs G, Taps t) {
+constexpr size_t az_smem() { return 2 * sizeof(float2) * AZSlab<S>::kArrays * (kAZT + 2 * R) * 32; }
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+struct AZSlabId {
+    int b, x0, y, z0;
+};
+__device__ __forceinline__ AZSlabId az_slab_of(const GroupArgs &G, int slab) {
+    const int b = find_brick(G.starts, G.nb, slab);
+    const BrickDev &B = G.bricks[b];
+    const int local = slab - __ldg(G.starts + b);
+    const int nzt = (B.nz + kAZT - 1) / kAZT, nxt = (B.nx + 31) / 32;
+    const int zt = local % nzt, rest = local / nzt;
+    return AZSlabId{b, (rest % nxt) * 32, rest / nxt, zt * kAZT};
+}
+
+// Issues the copies of one slab into `buf` (ROWS x 32 elements per array).
+template <int R, class S>
+__device__ __forceinline__ void az_issue(const GroupArgs &G, int slab, float2 *buf) {
+    constexpr int ROWS = kAZT + 2 * R;
+    using V4 = typename Store<S>::V4;
+    const AZSlabId id = az_slab_of(G, slab);
+    const BrickDev &B = G.bricks[id.b];
+    const int col = threadIdx.x & 31;
+    const long long pplane = (long long)B.px * B.ny;
+    const V4 *src = reinterpret_cast<const V4 *>(B.u4) + (long long)id.y * B.px + id.x0 + col;
+    for (int row = threadIdx.x >> 5; row < ROWS; row += kAZThreads / 32) {
+        const int zi = id.z0 - R + row;
+        const bool ok = (unsigned)zi < (unsigned)B.nz;
+        const V4 *g = src + (long long)(ok ? zi : 0) * pplane;
+        if constexpr (AZSlab<S>::kArrays == 2) {
+            cp_async8(buf + row * 32 + col, g, ok);
+            cp_async8(buf + (ROWS + row) * 32 + col, reinterpret_cast<const char *>(g) + 8, ok);
+        } else {
+            cp_async8(buf + row * 32 + col, g, ok);
+        }
+    }
+}
+
+template <int R, class S>
+__device__ __forceinline__ float2 az_read(const float2 *buf, int p, int i) {
+    constexpr int ROWS = kAZT + 2 * R;
+    if constexpr (AZSlab<S>::kArrays == 2) {
+        return buf[p * ROWS * 32 + i];
+    } else {
+        const uint2 w = reinterpret_cast<const uint2 *>(buf)[i];
+        return Store<S>::unpack2(p ? w.y : w.x);
+    }
+}
+
+template <int R, class S>
+__global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G, TapPairs t) {
     constexpr int T = 2 * R + 1;
     constexpr int ROWS = kAZT + 2 * R;
     constexpr int WIN = kAZO + 2 * R;
-    using V4 = typename Store<S>::V4;
+    constexpr int STAGE = AZSlab<S>::kArrays * ROWS * 32;  // float2 units
     using V2 = typename Store<S>::V2;
-    extern __shared__ float2 slab[];  // [2][ROWS][32]
-    const int b = find_brick(G.starts, G.nb, blockIdx.x);
-    const BrickDev &B = G.bricks[b];
-    const int local = blockIdx.x - __ldg(G.starts + b);
-    const int nzt = (B.nz + kAZT - 1) / kAZT, nxt = (B.nx + 31) / 32;
-    const int zt = local % nzt;
-    const int rest = local / nzt;
-    const int xt = rest % nxt, y = rest / nxt;
-    const int x0 = xt * 32, z0 = zt * kAZT;
-    const int px = B.px;
-    const long long pplane = (long long)px * B.ny;
-    const V4 *src = reinterpret_cast<const V4 *>(B.u4) + (long long)y * px + x0;
-
-    for (int i = threadIdx.x; i < ROWS * 32; i += kAZThreads) {
-        const int row = i >> 5, col = i & 31;
-        const int zi = z0 - R + row;
-        const float4 v = ((unsigned)zi < (unsigned)B.nz) ? Store<S>::unpack4(__ldg(src + (long long)zi * pplane + col))
-                                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-        slab[row * 32 + col] = make_float2(v.x, v.y);
-        slab[(ROWS + row) * 32 + col] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
+    extern __shared__ float2 slab[];  // [2 stages][arrays][ROWS][32]
+    const int total = __ldg(G.starts + G.nb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = x0 + lane;
-    const int zb = warp * kAZO;
-    if (x >= B.nx) return;
-    const float l1 = B.lambda1, l2 = B.lambda2;
-    float f1[kAZO];
-    {
-        float2 w[WIN];
+    int stage = 0;
+    if ((int)blockIdx.x < total) az_issue<R, S>(G, blockIdx.x, slab);
+    cp_async_commit();
+    for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
+        if (sl + (int)gridDim.x < total) az_issue<R, S>(G, sl + gridDim.x, slab + (stage ^ 1) * STAGE);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const float2 *buf = slab + stage * STAGE;
+        const AZSlabId id = az_slab_of(G, sl);
+        const BrickDev &B = G.bricks[id.b];
+        const int x = id.x0 + lane;
+        const int zb = warp * kAZO;
+        if (x < B.nx) {
+            const float l1 = B.lambda1, l2 = B.lambda2;
+            float f1[kAZO];
+            {
+                float2 w[WIN];
 #pragma unroll
-        for (int j = 0; j < WIN; ++j) w[j] = slab[(zb + j) * 32 + lane];
+                for (int j = 0; j < WIN; ++j) w[j] = az_read<R, S>(buf, 0, (zb + j) * 32 + lane);
 #pragma unroll
-        for (int o = 0; o < kAZO; ++o) {
-            float2 acc = make_float2(0.f, 0.f);
+                for (int o = 0; o < kAZO; ++o) {
+                    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < T; ++k) acc = f2fma(make_float2(t.g[k], t.g[k]), w[o + k], acc);
-            f1[o] = __fdividef(acc.x, acc.y);
-        }
-    }
-    float2 w[WIN];
+                    for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
+                    f1[o] = __fdividef(acc.x, acc.y);
+                }
+            }
+            float2 w[WIN];
 #pragma unroll
-    for (int j = 0; j < WIN; ++j) w[j] = slab[(ROWS + zb + j) * 32 + lane];
-    V2 *ab = reinterpret_cast<V2 *>(B.ab);
+            for (int j = 0; j < WIN; ++j) w[j] = az_read<R, S>(buf, 1, (zb + j) * 32 + lane);
+            const long long pplane = (long long)B.px * B.ny;
+            V2 *ab = reinterpret_cast<V2 *>(B.ab) + (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
+            float *const dump = B.dump;
 #pragma unroll
-    for (int o = 0; o < kAZO; ++o) {
-        const int zo = z0 + zb + o;
-        if (zo < B.nz) {
-            float2 acc = make_float2(0.f, 0.f);
+            for (int o = 0; o < kAZO; ++o) {
+                const int zo = id.z0 + zb + o;
+                if (zo < B.nz) {
+                    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < T; ++k) acc = f2fma(make_float2(t.g[k], t.g[k]), w[o + k], acc);
-            const float f2 = __fdividef(acc.x, acc.y);
-            ab[(long long)zo * pplane + (long long)y * px + x] =
-                Store<S>::pack2(make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2)));
-            if (B.dump) {
-                const long long q = (long long)zo * B.nx * B.ny + (long long)y * B.nx + x;
-                const long long n = (long long)B.nx * B.ny * B.nz;
-                B.dump[q] = f1[o] * B.cs[3] + B.cs[0];
-                B.dump[n + q] = f2 * B.cs[3] + B.cs[0];
+                    for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
+                    const float f2 = __fdividef(acc.x, acc.y);
+                    ab[o * pplane] =
+                        Store<S>::pack2(make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2)));
+                    if (dump) {
+                        const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
+                        const long long n = (long long)B.nx * B.ny * B.nz;
+                        dump[q] = f1[o] * B.cs[3] + B.cs[0];
+                        dump[n + q] = f2 * B.cs[3] + B.cs[0];
+                    }
+                }
             }
         }
+        __syncthreads();  // this stage is refilled by the next iteration's copies
+        stage ^= 1;
     }
 }
 
@@ -415,48 +502,66 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 4 : (R <= 8 ? 3 : 2)) k_t
 // argument kept in [0, 1]: for |u| < eps, atan(eps/|u|) = pi/2 - atan(|u|/eps).
 __device__ __forceinline__ float heaviside_q_fast(float u, float eps) {
     const float a = fabsf(u);
-    const float r = a >= eps ? atanf(__fdividef(eps, a)) * INV_PI : 0.5f - atanf(__fdividef(a, eps)) * INV_PI;
-    return copysignf(r, u);
+    const float at = atanf(__fdividef(fminf(a, eps), fmaxf(a, eps))) * INV_PI;
+    return copysignf(a >= eps ? at : 0.5f - at, u);
 }
 
-// z march over a 32x8 column tile of one brick, z chunk [z0, z0 + zc).
-// Output step zo:  store phi plane zo+3 (loaded into registers one step earlier)
-//                  and issue the loads of plane zo+4;  barrier;
-//                  normals of plane zo+2;  output of plane zo, which reads the
-//                  normals of zo-1, zo, zo+1 written in earlier steps.
-// Rings (logical plane p in slot p & (size-1)): phi 8 planes (zo-2 .. zo+3 live),
-// normals 4 planes (zo-1 .. zo+2 live).  The reflected tile offsets do not
-// depend on z and are computed once.  The (a, b) window is a register ring of
-// 2R+1+kPFB slots (plane s in slot s mod (2R+1+kPFB)); the load of plane
-// s+kPFB goes straight into its slot, so the body unrolled over the ring has
-// static indices.
+// z march over a 32x8 column tile of one brick, z chunk [z0, z0 + zc), two
+// output planes per step.  Planes are numbered relative to the chunk start
+// (r = z - z0); ring slots are r mod ring size, so with the step loop unrolled
+// over M planes every slot index is a compile-time constant.
+//
+// Step k, outputs zo = z0 + 2k and zo + 1:
+//   issue the (a, b) loads of the next step into the register ring; store phi
+//   planes zo+4, zo+5 (fetched one step earlier) into the phi ring and fetch
+//   zo+6, zo+7; barrier; normals of planes zo+3, zo+4; outputs zo, zo+1, which
+//   read phi zo-1 .. zo+2 and the normals of zo-1 .. zo+2 (earlier steps).
+// Ring sizes: phi 16 planes (one step reads zo-3 .. zo+5 across the barrier
+// while the next writes zo+6, zo+7), normals 8 (zo-1 .. zo+4 live), (a, b)
+// M = 16 or 32 register slots (2R+2 planes in use plus 2 in flight).
+// Finite differences use the logical planes, which hold reflect-101 copies
+// outside the brick; the unit normal is itself padded by reflect-101, so the
+// normal of plane -1 is that of plane 1 and the normal of plane nz that of
+// plane nz-2 (the prologue and the step loop copy them).
+template <int R>
+constexpr int tbz_ring() { return 2 * R + 4 <= 16 ? 16 : 32; }
+
+constexpr int kZPhiRing = 16, kZNrmRing = 8;
+constexpr int kZPW = kZX + 4, kZPH = kZY + 4;  // phi tile, halo 2
+constexpr int kZNW = kZX + 2, kZNH = kZY + 2;  // normal tile, halo 1
+constexpr size_t tbz_smem() {
+    return sizeof(float) * (kZPhiRing * kZPH * kZPW + kZNrmRing * 3 * kZNH * kZNW);
+}
+
 template <int R, class ImgT>
-__global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_tb_z(GroupArgs G, Taps t) {
+__global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G, TapPairs t) {
     constexpr int T = 2 * R + 1;
-    constexpr int M = T + kPFB;
-    constexpr int PW = kZX + 4, PH = kZY + 4;  // phi tile: halo 2
-    constexpr int NW = kZX + 2, NH = kZY + 2;  // normal tile: halo 1
+    constexpr int M = tbz_ring<R>();
+    constexpr int SPB = M / 2;  // steps per unrolled body
+    constexpr int PW = kZPW, PH = kZPH, NW = kZNW, NH = kZNH;
+    constexpr int PPL = PH * PW, NPL = 3 * NH * NW;
     constexpr int NPE = (PH * PW + kZThreads - 1) / kZThreads;
     constexpr int NNE = (NH * NW + kZThreads - 1) / kZThreads;
-    __shared__ float sphi[8][PH * PW];
-    __shared__ float snrm[4][3][NH * NW];
+    extern __shared__ float zsm[];
+    float *const sphi = zsm;                         // [kZPhiRing][PH * PW]
+    float *const snrm = zsm + kZPhiRing * PPL;       // [kZNrmRing][3][NH * NW]
 
     const int bi = find_brick(G.starts, G.nb, blockIdx.x);
-    const BrickDev &B = G.bricks[bi];
+    const BrickDev B = G.bricks[bi];
     const int local = blockIdx.x - __ldg(G.starts + bi);
     const int nbx = (B.nx + kZX - 1) / kZX, nby = (B.ny + kZY - 1) / kZY;
     const int bx = local % nbx, rr = local / nbx;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
     const long long plane = (long long)nx * ny;
-    const int zc = B.zc;
 
     const int tx = threadIdx.x & (kZX - 1), ty = threadIdx.x / kZX;
     const int x0 = bx * kZX, y0 = (rr % nby) * kZY;
     const int x = x0 + tx, y = y0 + ty;
     const bool active = x < nx && y < ny;
-    const int z0 = (rr / nby) * zc;
-    const int z1 = min(z0 + zc, nz);
-    const int nsteps = (z1 - z0) + 2 * R;
+    const int z0 = (rr / nby) * B.zc;
+    const int z1 = min(z0 + B.zc, nz);
+    const int nout = z1 - z0;
+    const int nplanes = nout + 2 * R;  // (a, b) planes of the chunk, r = -R .. nout + R - 1
     const long long col = (long long)min(y, ny - 1) * nx + min(x, nx - 1);
     const int px = B.px;
     const long long pplane = (long long)px * ny;
@@ -480,111 +585,147 @@ __global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_tb_z(GroupArgs G,
         const int qy = refl101(clampi(y0 + ly - 1, -1, ny), ny);
         noff[e] = clampi(qy - y0 + 2, 1, PH - 2) * PW + clampi(qx - x0 + 2, 1, PW - 2);
     }
-    auto fetch_phi = [&](int lz, float *v) {
-        const float *src = phi + (long long)refl101(clampi(lz, -2, nz + 1), nz) * plane;
+    // phi plane z (logical, -2 .. nz+1 hold reflect-101 copies) into registers / the ring
+    auto fetch_phi = [&](int z, float *v) {
+        const float *src = phi + (long long)refl101(clampi(z, -2, nz + 1), nz) * plane;
 #pragma unroll
         for (int e = 0; e < NPE; ++e) v[e] = __ldg(src + poff[e]);
     };
-    auto store_phi = [&](int lz, const float *v) {
-        float *dst = sphi[lz & 7];
+    auto store_phi = [&](float *dst, const float *v) {
 #pragma unroll
         for (int e = 0; e < NPE; ++e)
             if ((int)threadIdx.x + e * kZThreads < PH * PW) dst[threadIdx.x + e * kZThreads] = v[e];
     };
-    auto normals = [&](int lz) {
-        const int q = refl101(clampi(lz, -1, nz), nz);  // physical plane; q-1..q+1 are in the phi ring
-        const float *pm = sphi[(q - 1) & 7], *pc = sphi[q & 7], *pp = sphi[(q + 1) & 7];
-        float *n0 = snrm[lz & 3][0], *n1 = snrm[lz & 3][1], *n2 = snrm[lz & 3][2];
+    // unit normals of one plane from phi planes pm, pc, pp of the ring; the
+    // central differences' factor 1/2 cancels: d / (|d| + 2e-10) = (d/2) / (|d/2| + 1e-10)
+    auto normals = [&](const float *pm, const float *pc, const float *pp, float *dst) {
 #pragma unroll
         for (int e = 0; e < NNE; ++e) {
             const int i = threadIdx.x + e * kZThreads;
             if (i < NH * NW) {
                 const int o = noff[e];
-                const float gx = (pc[o + 1] - pc[o - 1]) * 0.5f;
-                const float gy = (pc[o + PW] - pc[o - PW]) * 0.5f;
-                const float gz = (pp[o] - pm[o]) * 0.5f;
-                const float inv = rcp_approx(sqrt_approx(gx * gx + gy * gy + gz * gz) + 1e-10f);
-                n0[i] = gx * inv;
-                n1[i] = gy * inv;
-                n2[i] = gz * inv;
+                const float gx = pc[o + 1] - pc[o - 1];
+                const float gy = pc[o + PW] - pc[o - PW];
+                const float gz = pp[o] - pm[o];
+                const float inv = rcp_approx(sqrt_approx(gx * gx + gy * gy + gz * gz) + 2e-10f);
+                dst[i] = gx * inv;
+                dst[NH * NW + i] = gy * inv;
+                dst[2 * NH * NW + i] = gz * inv;
             }
         }
     };
+    auto copy_normals = [&](const float *src, float *dst) {
+#pragma unroll
+        for (int e = 0; e < NNE; ++e) {
+            const int i = threadIdx.x + e * kZThreads;
+            if (i < NH * NW) {
+                dst[i] = src[i];
+                dst[NH * NW + i] = src[NH * NW + i];
+                dst[2 * NH * NW + i] = src[2 * NH * NW + i];
+            }
+        }
+    };
+    auto phi_at = [&](int r) { return sphi + ((r + kZPhiRing) & (kZPhiRing - 1)) * PPL; };
+    auto nrm_at = [&](int r) { return snrm + ((r + kZNrmRing) & (kZNrmRing - 1)) * NPL; };
 
-    float pv[NPE];
-    for (int lz = z0 - 2; lz <= z0 + 3; ++lz) {
-        fetch_phi(lz, pv);
-        store_phi(lz, pv);
+    // prologue: phi planes z0-2 .. z0+3, normals z0-1 .. z0+2 (physical mapping at the faces)
+    {
+        float pv[NPE];
+        for (int r = -2; r <= 3; ++r) {
+            fetch_phi(z0 + r, pv);
+            store_phi(phi_at(r), pv);
+        }
     }
     __syncthreads();
-    normals(z0 - 1);
-    normals(z0);
-    normals(z0 + 1);
-    fetch_phi(z0 + 3, pv);  // the first output step stores plane z0+3 again, from registers
+    for (int r = -1; r <= 2; ++r) {
+        const int q = refl101(clampi(z0 + r, -1, nz), nz) - z0;  // physical plane, relative
+        normals(phi_at(q - 1), phi_at(q), phi_at(q + 1), nrm_at(r));
+    }
+    float pva[NPE], pvb[NPE];
+    fetch_phi(z0 + 4, pva);
+    fetch_phi(z0 + 5, pvb);
 
     const float pxy = active ? __ldg(B.prof + x) * __ldg(B.prof + nx + y) : 0.f;
-    const float *profz = B.prof + nx + ny;
+    const float *profz = B.prof + nx + ny + z0;
     const float l12 = B.lambda1 - B.lambda2, s2 = B.cs[2];
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
     const float eps = B.eps, eps_pi = eps * INV_PI, eps2 = eps * eps;
     const float mu = B.mu, nu = B.nu, dt = B.dt;
-    const ImgT *img = reinterpret_cast<const ImgT *>(B.img);
-    long long qz = (long long)z0 * plane + col;  // this thread's voxel index at the output plane
-    float *phi_out = par ? B.phi[0] : B.phi[1];
-    float *q_out = par ? B.q[0] : B.q[1];
+    const ImgT *img = reinterpret_cast<const ImgT *>(B.img) + col;
+    float *phi_out = (par ? B.phi[0] : B.phi[1]) + col;
+    float *q_out = (par ? B.q[0] : B.q[1]) + col;
+    float *const dump = B.dump;
+    const long long n = plane * nz;
 
+    // (a, b) plane r = -R + s of the chunk, s = 0 .. nplanes-1; zero outside the brick
     const float2 *src = B.abxy + (long long)min(y, ny - 1) * px + min(x, nx - 1);
     auto load = [&](int s) -> float2 {
         const int zi = z0 - R + s;
-        return (active && s < nsteps && (unsigned)zi < (unsigned)nz) ? __ldg(src + (long long)zi * pplane)
-                                                                      : make_float2(0.f, 0.f);
+        return (active && s < nplanes && (unsigned)zi < (unsigned)nz) ? __ldg(src + (long long)zi * pplane)
+                                                                       : make_float2(0.f, 0.f);
     };
-    float2 r[M];
+    float2 ring[M];
 #pragma unroll
-    for (int i = 0; i < kPFB; ++i) r[i] = load(i);
-    float iv = active ? centred(img, qz, inv_s, nms) : 0.f;
-    for (int base = 0; base < nsteps; base += M) {
+    for (int s = 0; s < 2 * R + 2; ++s) ring[s] = load(s);
+    float iv0 = active ? centred(img, (long long)z0 * plane, inv_s, nms) : 0.f;
+    float iv1 = (active && nout > 1) ? centred(img, (long long)(z0 + 1) * plane, inv_s, nms) : 0.f;
+
+    for (int base = 0; 2 * base < nout; base += SPB) {
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            const int s = base + j;
-            if (s < nsteps) {
-                r[(j + kPFB) % M] = load(s + kPFB);
-                if (s >= 2 * R) {
-                    const int zo = z0 + s - 2 * R;
-                    store_phi(zo + 3, pv);
-                    fetch_phi(zo + 4, pv);
-                    const float im = iv;
-                    if (active && zo + 1 < z1) iv = centred(img, qz + plane, inv_s, nms);
-                    __syncthreads();
-                    normals(zo + 2);
-                    if (active) {
+        for (int kk = 0; kk < SPB; ++kk) {
+            const int k = base + kk;
+            const int r0 = 2 * k;          // relative output plane
+            if (r0 < nout) {
+                const int zo = z0 + r0;
+                // loads of the next step: (a, b) planes s = 2k + 2R + 2, +3
+                ring[(2 * kk + 2 * R + 2) % M] = load(r0 + 2 * R + 2);
+                ring[(2 * kk + 2 * R + 3) % M] = load(r0 + 2 * R + 3);
+                store_phi(phi_at(2 * kk + 4), pva);
+                store_phi(phi_at(2 * kk + 5), pvb);
+                fetch_phi(zo + 6, pva);
+                fetch_phi(zo + 7, pvb);
+                const float im0 = iv0, im1 = iv1;
+                if (active && r0 + 2 < nout) iv0 = centred(img, (long long)(zo + 2) * plane, inv_s, nms);
+                if (active && r0 + 3 < nout) iv1 = centred(img, (long long)(zo + 3) * plane, inv_s, nms);
+                __syncthreads();
+#pragma unroll
+                for (int c = 3; c <= 4; ++c) {
+                    if (zo + c < nz)
+                        normals(phi_at(2 * kk + c - 1), phi_at(2 * kk + c), phi_at(2 * kk + c + 1), nrm_at(2 * kk + c));
+                    else if (zo + c == nz)
+                        copy_normals(nrm_at(2 * kk + c - 2), nrm_at(2 * kk + c));
+                }
+                if (active) {
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (c == 1 && r0 + 1 >= nout) break;
                         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int k = 0; k < T; ++k)
-                            acc = f2fma(make_float2(t.g[k], t.g[k]), r[(j - 2 * R + k + 2 * M) % M], acc);
-                        const float K1 = pxy * __ldg(profz + zo);
+                        for (int kt = 0; kt < T; ++kt) acc = f2fma(t.g[kt], ring[(2 * kk + c + kt) % M], acc);
+                        const float im = c ? im1 : im0;
+                        const float K1 = pxy * __ldg(profz + r0 + c);
                         const float g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
-                        const float *p0 = sphi[zo & 7];
+                        const float *p0 = phi_at(2 * kk + c);
                         const int pc0 = (ty + 2) * PW + tx + 2;
                         const float ph = p0[pc0];
                         const float lap = (p0[pc0 + 1] + p0[pc0 - 1] - 2.f * ph) + (p0[pc0 + PW] + p0[pc0 - PW] - 2.f * ph) +
-                                          (sphi[(zo + 1) & 7][pc0] + sphi[(zo - 1) & 7][pc0] - 2.f * ph);
+                                          (phi_at(2 * kk + c + 1)[pc0] + phi_at(2 * kk + c - 1)[pc0] - 2.f * ph);
                         const int nc0 = (ty + 1) * NW + tx + 1;
-                        const float *n0 = snrm[zo & 3][0], *n1 = snrm[zo & 3][1];
-                        const float kap = (n0[nc0 + 1] - n0[nc0 - 1]) * 0.5f + (n1[nc0 + NW] - n1[nc0 - NW]) * 0.5f +
-                                          (snrm[(zo + 1) & 3][2][nc0] - snrm[(zo - 1) & 3][2][nc0]) * 0.5f;
+                        const float *nn = nrm_at(2 * kk + c);
+                        const float kap = ((nn[nc0 + 1] - nn[nc0 - 1]) + (nn[NH * NW + nc0 + NW] - nn[NH * NW + nc0 - NW]) +
+                                           (nrm_at(2 * kk + c + 1)[2 * NH * NW + nc0] -
+                                            nrm_at(2 * kk + c - 1)[2 * NH * NW + nc0])) * 0.5f;
                         const float del = eps_pi * rcp_approx(eps2 + ph * ph);  // Eq. (14)
                         const float pn = ph + dt * (mu * (lap - kap) + del * (nu * kap - g));
+                        const long long qz = (long long)(zo + c) * plane;
                         phi_out[qz] = pn;
                         q_out[qz] = heaviside_q_fast(pn, eps);
-                        if (B.dump) {
-                            const long long n = (long long)nx * ny * nz;
-                            B.dump[2 * n + qz] = g;
-                            B.dump[3 * n + qz] = kap;
-                            B.dump[4 * n + qz] = lap;
+                        if (dump) {
+                            dump[2 * n + col + qz] = g;
+                            dump[3 * n + col + qz] = kap;
+                            dump[4 * n + col + qz] = lap;
                         }
                     }
-                    qz += plane;
                 }
             }
         }
@@ -595,6 +736,14 @@ __global__ void __launch_bounds__(kZThreads, R <= 8 ? 3 : 2) k_tb_z(GroupArgs G,
 
 // The update kernel (storage independent; defined in rsf_tiled_f32.cu).
 cudaError_t launch_tb_z(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
+cudaError_t prepare_tb_z(int R);
+
+// Resident CTAs of the persistent z kernel of group A (set by prepare_storage).
+template <int R, class S>
+int &az_persist() {
+    static int n = 152;
+    return n;
+}
 
 template <int R, class S>
 cudaError_t prepare_storage() {
@@ -605,8 +754,16 @@ cudaError_t prepare_storage() {
                                   (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_ta_xy<R, float, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_ta_z<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)az_smem<R>())) !=
+    if ((e = cudaFuncSetAttribute(k_ta_z<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)az_smem<R, S>())) !=
         cudaSuccess) return e;
+    {
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ta_z<R, S>, kAZThreads, az_smem<R, S>())) !=
+            cudaSuccess) return e;
+        az_persist<R, S>() = sms * (occ > 0 ? occ : 1);
+    }
     return cudaFuncSetAttribute(k_tb_xy<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)XYLayout<R, 1>::bytes);
 }
@@ -614,26 +771,28 @@ cudaError_t prepare_storage() {
 template <int R, class S>
 cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
     GroupArgs G{g.bricks, nullptr, g.nb, parity};
+    const TapPairs tp = tap_pairs(g.taps);
     {
         ProfScope ps(prof, KID_TA_XY);
         G.starts = g.starts[0];
         constexpr size_t sm = XYLayout<R, 2>::bytes;
         switch (g.imgtype) {
-            case 0: k_ta_xy<R, uint8_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, g.taps); break;
-            case 1: k_ta_xy<R, uint16_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, g.taps); break;
-            default: k_ta_xy<R, float, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, g.taps);
+            case 0: k_ta_xy<R, uint8_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
+            case 1: k_ta_xy<R, uint16_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
+            default: k_ta_xy<R, float, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp);
         }
     }
     {
         ProfScope ps(prof, KID_TA_Z);
         G.starts = g.starts[1];
-        k_ta_z<R, S><<<g.ncta[1], kAZThreads, az_smem<R>(), s>>>(G, g.taps);
+        const unsigned grid = g.ncta[1] < (unsigned)az_persist<R, S>() ? g.ncta[1] : (unsigned)az_persist<R, S>();
+        k_ta_z<R, S><<<grid, kAZThreads, az_smem<R, S>(), s>>>(G, tp);
     }
     {
         ProfScope ps(prof, KID_TB_XY);
         G.starts = g.starts[2];
         constexpr size_t sm = XYLayout<R, 1>::bytes;
-        k_tb_xy<R, S><<<g.ncta[2], kXYThreads, sm, s>>>(G, g.taps);
+        k_tb_xy<R, S><<<g.ncta[2], kXYThreads, sm, s>>>(G, tp);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

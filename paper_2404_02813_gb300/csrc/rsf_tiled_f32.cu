@@ -11,8 +11,17 @@ template <int R, class ImgT>
 cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
     GroupArgs G{g.bricks, g.starts[3], g.nb, parity};
     ProfScope ps(prof, KID_TB_Z);
-    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, 0, s>>>(G, g.taps);
+    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem(), s>>>(G, tap_pairs(g.taps));
     return cudaGetLastError();
+}
+template <int R>
+cudaError_t prepare_bz_i() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem())) !=
+        cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem())) !=
+        cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tb_z<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem());
 }
 template <int R>
 cudaError_t launch_bz_i(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
@@ -27,6 +36,20 @@ __global__ void k_q_init(const float *__restrict__ phi, float *__restrict__ q, l
         q[i] = heaviside_q_fast(__ldg(phi + i), eps);
 }
 }  // namespace
+
+cudaError_t prepare_tb_z(int R) {
+    switch (R) {
+        case 2: return prepare_bz_i<2>();
+        case 3: return prepare_bz_i<3>();
+        case 4: return prepare_bz_i<4>();
+        case 5: return prepare_bz_i<5>();
+        case 6: return prepare_bz_i<6>();
+        case 8: return prepare_bz_i<8>();
+        case 10: return prepare_bz_i<10>();
+        case 12: return prepare_bz_i<12>();
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_tb_z(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
     switch (g.taps.R) {
@@ -64,6 +87,8 @@ cudaError_t tiled_prepare_f16(int R);
 cudaError_t tiled_prepare_bf16(int R);
 
 cudaError_t tiled_prepare(int storage, int R) {
+    const cudaError_t e = tiled::prepare_tb_z(R);
+    if (e != cudaSuccess) return e;
     switch (storage) {
         case 0: return tiled::prepare_group_s<float>(R);
         case 1: return tiled_prepare_bf16(R);
