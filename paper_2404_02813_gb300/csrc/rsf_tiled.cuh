@@ -385,21 +385,36 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 struct AZSlabId {
     int b, x0, y, z0;
 };
+// n / d and n % d for n >= 0, d > 0.  Below 2^24 a float quotient, off by at
+// most one, corrected once; larger n (very thin bricks only) divide exactly.
+__device__ __forceinline__ int divmod24(int n, int d, float inv_d, int &rem) {
+    if (n >= (1 << 24)) {
+        const int q = n / d;
+        rem = n - q * d;
+        return q;
+    }
+    int q = __float2int_rz((float)n * inv_d);
+    int r = n - q * d;
+    if (r < 0) { --q; r += d; } else if (r >= d) { ++q; r -= d; }
+    rem = r;
+    return q;
+}
 __device__ __forceinline__ AZSlabId az_slab_of(const GroupArgs &G, int slab) {
     const int b = find_brick(G.starts, G.nb, slab);
     const BrickDev &B = G.bricks[b];
     const int local = slab - __ldg(G.starts + b);
     const int nzt = (B.nz + kAZT - 1) / kAZT, nxt = (B.nx + 31) / 32;
-    const int zt = local % nzt, rest = local / nzt;
-    return AZSlabId{b, (rest % nxt) * 32, rest / nxt, zt * kAZT};
+    int zt, xt;
+    const int rest = divmod24(local, nzt, __frcp_rn((float)nzt), zt);
+    const int y = divmod24(rest, nxt, __frcp_rn((float)nxt), xt);
+    return AZSlabId{b, xt * 32, y, zt * kAZT};
 }
 
 // Issues the copies of one slab into `buf` (ROWS x 32 elements per array).
 template <int R, class S>
-__device__ __forceinline__ void az_issue(const GroupArgs &G, int slab, float2 *buf) {
+__device__ __forceinline__ void az_issue(const GroupArgs &G, const AZSlabId &id, float2 *buf) {
     constexpr int ROWS = kAZT + 2 * R;
     using V4 = typename Store<S>::V4;
-    const AZSlabId id = az_slab_of(G, slab);
     const BrickDev &B = G.bricks[id.b];
     const int col = threadIdx.x & 31;
     const long long pplane = (long long)B.px * B.ny;
@@ -439,15 +454,22 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
     const int total = __ldg(G.starts + G.nb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int stage = 0;
-    if ((int)blockIdx.x < total) az_issue<R, S>(G, blockIdx.x, slab);
+    AZSlabId next{};
+    if ((int)blockIdx.x < total) {
+        next = az_slab_of(G, blockIdx.x);
+        az_issue<R, S>(G, next, slab);
+    }
     cp_async_commit();
     for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
-        if (sl + (int)gridDim.x < total) az_issue<R, S>(G, sl + gridDim.x, slab + (stage ^ 1) * STAGE);
+        const AZSlabId id = next;
+        if (sl + (int)gridDim.x < total) {
+            next = az_slab_of(G, sl + gridDim.x);
+            az_issue<R, S>(G, next, slab + (stage ^ 1) * STAGE);
+        }
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
         const float2 *buf = slab + stage * STAGE;
-        const AZSlabId id = az_slab_of(G, sl);
         const BrickDev &B = G.bricks[id.b];
         const int x = id.x0 + lane;
         const int zb = warp * kAZO;
@@ -498,11 +520,27 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
 
 // ------------------------------------------------------------------ B: z
 
-// q = +-atan(eps/|u|)/pi (the small side of H, sign of u), with the atan
-// argument kept in [0, 1]: for |u| < eps, atan(eps/|u|) = pi/2 - atan(|u|/eps).
+// q = +-atan(eps/|u|)/pi (the small side of H, sign of u) with the atan
+// argument kept in [0, 1]: atan(m/M) for m = min(|u|, eps), M = max(|u|, eps),
+// and for |u| < eps, atan(eps/|u|) = pi/2 - atan(|u|/eps).  atan(x)/pi on
+// [0, 1] is x P(x^2), P the degree-8 minimax polynomial of relative error
+// (coefficients by Lawson's algorithm, atan_poly.py), 1.5e-7 relative in FP32.
+__device__ __forceinline__ float atan01_pi(float x) {
+    const float t = x * x;
+    float p = 9.071480017e-04f;
+    p = fmaf(p, t, -5.114803091e-03f);
+    p = fmaf(p, t, 1.358913258e-02f);
+    p = fmaf(p, t, -2.388691157e-02f);
+    p = fmaf(p, t, 3.387114406e-02f);
+    p = fmaf(p, t, -4.521160573e-02f);
+    p = fmaf(p, t, 6.363848597e-02f);
+    p = fmaf(p, t, -1.061024666e-01f);
+    p = fmaf(p, t, 3.183098733e-01f);
+    return x * p;
+}
 __device__ __forceinline__ float heaviside_q_fast(float u, float eps) {
     const float a = fabsf(u);
-    const float at = atanf(__fdividef(fminf(a, eps), fmaxf(a, eps))) * INV_PI;
+    const float at = atan01_pi(__fdividef(fminf(a, eps), fmaxf(a, eps)));
     return copysignf(a >= eps ? at : 0.5f - at, u);
 }
 
