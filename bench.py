@@ -53,7 +53,11 @@ SETUP_LAUNCHES = 3  # statistics, their reduction, centring
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "f908fef1f273ff37",
+        "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
+    for k, v in {"rsf_ta_xy": 20.99, "rsf_ta_z": 23.42, "rsf_tb_xy": 15.19, "rsf_tb_z": 21.89}.items()
+}
 
 P_LIGHTSHEET = 4300.0
 
@@ -558,8 +562,9 @@ def main():
         algo = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2)[dom] * n_vox
         achieved = algo / avg_s / 1e9
         tr = NCU_TRAFFIC.get(dom)
+        same_case = args.storage == "f32" and vol.dtype == np.uint16 and params["sigma"] == 3.0
         traffic = (tr["bytes_per_voxel"] * n_vox
-                   if tr and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
+                   if tr and same_case and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
         launches = SETUP_LAUNCHES * args.steps + sum(n for n, _ in prof.values())
         line = {
             "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
