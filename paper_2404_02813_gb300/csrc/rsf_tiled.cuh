@@ -43,7 +43,7 @@ namespace tiled {
 
 constexpr int kXYT = 32;          // x/y kernel: output tile edge (x and y)
 constexpr int kXYThreads = 256;   // 8 warps
-constexpr int kXYPlanes = 8;      // z-planes per CTA of the x/y kernel
+constexpr int kXYPlanes = 16;      // z-planes per CTA of the x/y kernel
 constexpr int kZX = 32, kZY = 8;  // z march: columns per CTA
 constexpr int kZThreads = kZX * kZY;
 constexpr int kAZT = 64;          // x-z slab: output planes per CTA
