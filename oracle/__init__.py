@@ -77,7 +77,7 @@ def _lib(omp: bool = False):
     lib.rsf_oracle_step.restype = None
     lib.rsf_oracle_evolve.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, ctypes.c_int]
     lib.rsf_oracle_evolve.restype = None
-    lib.rsf_oracle_point_next.argtypes = [dp, dp, i64, i64, i64, i64, i64, i64, d, d, d, d, d, d, d]
+    lib.rsf_oracle_point_next.argtypes = [dp, dp, i64, i64, i64, i64, i64, i64, d, d, d, d, d, d, d, dp]
     lib.rsf_oracle_point_next.restype = d
     lib.rsf_oracle_dump_slots.argtypes = []
     lib.rsf_oracle_dump_slots.restype = ctypes.c_int
@@ -171,10 +171,17 @@ def evolve(I, phi0, params: dict, iters: int, omp: bool = False) -> np.ndarray:
     return out
 
 
-def point_next(I, phi, params: dict, x: int, y: int, z: int) -> float:
-    """phi_{n+1} at voxel (x, y, z) by direct triple sums (no separable passes)."""
+POINT_TERMS = ("e1", "e2", "g", "kappa", "lap")
+
+
+def point_next(I, phi, params: dict, x: int, y: int, z: int, terms: bool = False):
+    """phi_{n+1} at voxel (x, y, z) by direct triple sums (no separable passes).
+
+    With ``terms``, returns (phi_next, {e1, e2, g, kappa, lap}) at the voxel."""
     I = _vol(I)
     phi = _vol(phi)
     nz, ny, nx = I.shape
-    return float(_lib().rsf_oracle_point_next(_dp(I), _dp(phi), nx, ny, nz, int(x), int(y), int(z),
-                                              *_params(params)))
+    t = np.zeros(len(POINT_TERMS), dtype=np.float64)
+    v = float(_lib().rsf_oracle_point_next(_dp(I), _dp(phi), nx, ny, nz, int(x), int(y), int(z),
+                                           *_params(params), _dp(t) if terms else None))
+    return (v, dict(zip(POINT_TERMS, t.tolist()))) if terms else v

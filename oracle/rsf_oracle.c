@@ -316,7 +316,8 @@ void rsf_oracle_evolve(const double *I, const double *phi0, double *phi_out,
  * the full oracle, and as an independent check of rsf_oracle_step. */
 double rsf_oracle_point_next(const double *I, const double *phi, i64 nx, i64 ny, i64 nz,
                              i64 px, i64 py, i64 pz, double sigma, double eps,
-                             double lambda1, double lambda2, double nu, double mu, double dt)
+                             double lambda1, double lambda2, double nu, double mu, double dt,
+                             double *terms)
 {
     double g[256];
     int R = rsf_oracle_taps(sigma, g);
@@ -395,5 +396,12 @@ double rsf_oracle_point_next(const double *I, const double *phi, i64 nx, i64 ny,
         lap += at_refl(phi, u[0], u[1], u[2], nx, ny, nz) + at_refl(phi, v[0], v[1], v[2], nx, ny, nz) - 2.0 * c0;
     }
     double del = rsf_oracle_dirac(c0, eps);
+    if (terms) {  /* e1, e2, g, kappa, L at the voxel */
+        terms[0] = e1;
+        terms[1] = e2;
+        terms[2] = gg;
+        terms[3] = kap;
+        terms[4] = lap;
+    }
     return c0 + dt * (mu * (lap - kap) + del * (nu * kap - gg));
 }

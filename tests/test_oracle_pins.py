@@ -285,6 +285,12 @@ def test_step_matches_brute_force(shape, sigma, seed):
     # the voxel-at-a-time evaluation with direct sums agrees as well
     for (z, y, x) in [(0, 0, 0), (shape[0] - 1, 2, shape[2] - 1), (3, 4, 5)]:
         assert abs(oracle.point_next(I, phi, p, x, y, z) - ref[z, y, x]) < 1e-9 * max(1.0, abs(ref[z, y, x]))
+    # and its intermediate terms equal the separable step's stage fields
+    _, dump = oracle.step(I, phi, p, dump=True)
+    for (z, y, x) in [(0, 0, 0), (3, 4, 5)]:
+        _, t = oracle.point_next(I, phi, p, x, y, z, terms=True)
+        for k in ("e1", "e2", "g", "kappa", "lap"):
+            assert abs(t[k] - dump[k][z, y, x]) <= 1e-9 * max(1.0, abs(dump[k][z, y, x])), k
 
 
 def test_step_constant_phi_reduces_to_force_only():
