@@ -48,7 +48,8 @@ def algo_bytes_per_voxel(img: int, st: int) -> dict:
     }
 
 
-SETUP_LAUNCHES = 3  # statistics, their reduction, centring
+SETUP_LAUNCHES = 3  # statistics, their reduction, q of phi0
+NOMINAL_HBM_GBS = 7900.0
 
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
@@ -146,6 +147,11 @@ class ClockSampler:
 def make_workload(name: str, rank: int, size=None, iters_override=None):
     from paper_2404_02813_gb300 import synth
     e = size or 512
+    if name == "milling1024":
+        e = size or 1024
+        vol = synth.field_volume(synth.MillingField(extent_xyz=(e, e, e), workload=4 + 100 * rank))
+        params = synth.RSFParams().as_dict()
+        return vol, synth.mean_rule_phi0(vol), params, iters_override or 300
     if name == "lightsheet512":
         vol = synth.lightsheet_volume_u16((e, e, e), brick=rank)
         params = dict(sigma=3.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P_LIGHTSHEET ** 2, mu=1.0, dt=0.1)
@@ -405,6 +411,25 @@ def workload_desc(name, vol, params, iters):
             "l2": "inputs larger than L2 (each FP32 field 4*voxels bytes)"}
 
 
+def cpu_baseline_omp(vol, phi0, params, budget_s=10.0):
+    """The same oracle source built with OpenMP (loops over independent outputs split
+    across all host cores, bit-identical results) on a bounded 128^3 crop."""
+    import oracle
+    c = min(128, *vol.shape)
+    I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
+    ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
+    t0 = time.perf_counter()
+    oracle.evolve(I, ph, params, 1, omp=True)
+    t1 = time.perf_counter() - t0
+    its = max(1, min(20, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.evolve(I, ph, params, its, omp=True)
+    dt = time.perf_counter() - t0
+    return {"value": I.size * its / dt / 1e9, "unit": "GVoxel-iterations/s", "cores": os.cpu_count(),
+            "kind": "oracle (OpenMP build)",
+            "sample": f"{c}^3 corner crop of the workload volume, {its} iterations, FP64 C (-O2, OpenMP)"}
+
+
 def cpu_baseline(vol, phi0, params, budget_s=15.0):
     """The FP64 oracle (single thread) on a bounded corner crop of the same volume."""
     import oracle
@@ -463,7 +488,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsf", choices=["rsf", "reference"])
     ap.add_argument("--workload", default="lightsheet512",
-                    choices=["lightsheet512", "lightsheet512_s5", "tree64", "bricks256", "serve"])
+                    choices=["lightsheet512", "lightsheet512_s5", "tree64", "milling1024", "bricks256", "serve"])
     ap.add_argument("--requests", type=int, default=200, help="requests per arrival rate (serve)")
     ap.add_argument("--rates", default="8,16,24,32", help="Poisson arrival rates in requests/s (serve)")
     ap.add_argument("--bricks", type=int, default=None, help="number of bricks of the batched workload")
@@ -554,6 +579,20 @@ def main():
                "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + ph.numel() * 4),
                "d2h_bytes_per_step": int(oh.numel() * 4)}
 
+    # 16-bit storage against FP32 storage on the same volume (reported, not timed)
+    vs_fp32 = None
+    if args.workload == "milling1024" and args.storage != "f32":
+        ctx.set_storage("f32")
+        ref32 = ctx.evolve(v, ph0, params, iters)
+        ctx.set_storage(args.storage)
+        a, b = out > 0, ref32 > 0
+        inter = float(torch.logical_and(a, b).sum().item())
+        vs_fp32 = {"sign_disagreement": float((a != b).float().mean().item()),
+                   "dice": 2.0 * inter / max(float(a.sum().item() + b.sum().item()), 1.0),
+                   "max_abs_dphi": float((out - ref32).abs().max().item()),
+                   "note": f"{args.storage} storage vs FP32 storage, both on the GPU, after {iters} iterations"}
+        del ref32
+
     if rank == 0:
         peak, peak_kind = peaks()
         dom = max(prof, key=lambda k: prof[k][1])
@@ -561,6 +600,8 @@ def main():
         avg_s = tot_ms / max(n_l, 1) / 1e3
         algo = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2)[dom] * n_vox
         achieved = algo / avg_s / 1e9
+        per_kernel = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2)
+        sched_bytes = sum(per_kernel[k] for k, (n, _) in prof.items() if n and k in per_kernel)
         tr = NCU_TRAFFIC.get(dom)
         same_case = args.storage == "f32" and vol.dtype == np.uint16 and params["sigma"] == 3.0
         traffic = (tr["bytes_per_voxel"] * n_vox
@@ -576,16 +617,22 @@ def main():
                            parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                         "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic": traffic, "algo_bytes_per_launch": algo,
-                         "avg_launch_ms": avg_s * 1e3, "launches": n_l},
+                         "avg_launch_ms": avg_s * 1e3, "launches": n_l,
+                         "schedule_bytes_per_voxel_iteration": sched_bytes,
+                         "model_ceiling_gvox_it_s": peak / sched_bytes},
             "kernels": {k: {"launches": n, "ms": round(m, 3), "share": round(m / max(sum(x[1] for x in prof.values()), 1e-9), 4)}
                         for k, (n, m) in prof.items() if n},
             "clocks": clk,
             "gpu_launches": launches,
             "e2e": e2e,
         }
+        if vs_fp32 is not None:
+            line["vs_fp32"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(vol, phi0, params)
+            line["cpu_baseline_omp"] = cpu_baseline_omp(vol, phi0, params)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

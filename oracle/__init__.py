@@ -73,11 +73,12 @@ def _lib(omp: bool = False):
     lib.rsf_oracle_dirac.restype = d
     lib.rsf_oracle_stencils.argtypes = [dp, i64, i64, i64, dp, dp]
     lib.rsf_oracle_stencils.restype = None
-    lib.rsf_oracle_step.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, dp]
+    lib.rsf_oracle_step.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, dp, ctypes.c_int]
     lib.rsf_oracle_step.restype = None
-    lib.rsf_oracle_evolve.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, ctypes.c_int]
+    lib.rsf_oracle_evolve.argtypes = [dp, dp, dp, i64, i64, i64, d, d, d, d, d, d, d, ctypes.c_int, ctypes.c_int]
     lib.rsf_oracle_evolve.restype = None
-    lib.rsf_oracle_point_next.argtypes = [dp, dp, i64, i64, i64, i64, i64, i64, d, d, d, d, d, d, d, dp]
+    lib.rsf_oracle_point_next.argtypes = [dp, dp, i64, i64, i64, i64, i64, i64, d, d, d, d, d, d, d, dp,
+                                          ctypes.c_int]
     lib.rsf_oracle_point_next.restype = d
     lib.rsf_oracle_dump_slots.argtypes = []
     lib.rsf_oracle_dump_slots.restype = ctypes.c_int
@@ -142,7 +143,18 @@ def _params(p: dict):
             float(p["nu"]), float(p["mu"]), float(p["dt"]))
 
 
-def step(I, phi, params: dict, dump: bool = False, omp: bool = False):
+# Data-term forms: "li" (Li et al.'s e_i with K*1 and K*f_i, Eqs. 11-12 as read)
+# and "eq15" (the paper's Eq. 15 with sigma_2 = 0: e_i = (I - f_i)^2).
+FORCES = {"li": 0, "eq15": 1}
+
+
+def _force(force: str) -> int:
+    if force not in FORCES:
+        raise ValueError(f"unknown force form {force!r}; expected one of {sorted(FORCES)}")
+    return FORCES[force]
+
+
+def step(I, phi, params: dict, dump: bool = False, omp: bool = False, force: str = "li"):
     """One iteration. Returns phi_next, or (phi_next, {stage: array}) with ``dump``."""
     I = _vol(I)
     phi = _vol(phi)
@@ -154,27 +166,28 @@ def step(I, phi, params: dict, dump: bool = False, omp: bool = False):
     nslots = lib.rsf_oracle_dump_slots()
     buf: Optional[np.ndarray] = np.empty((nslots,) + I.shape, dtype=np.float64) if dump else None
     lib.rsf_oracle_step(_dp(I), _dp(phi), _dp(out), nx, ny, nz, *_params(params),
-                        _dp(buf) if dump else None)
+                        _dp(buf) if dump else None, _force(force))
     if dump:
         return out, {name: buf[i] for i, name in enumerate(DUMP_NAMES)}
     return out
 
 
-def evolve(I, phi0, params: dict, iters: int, omp: bool = False) -> np.ndarray:
+def evolve(I, phi0, params: dict, iters: int, omp: bool = False, force: str = "li") -> np.ndarray:
     I = _vol(I)
     phi0 = _vol(phi0)
     if I.shape != phi0.shape:
         raise ValueError("I and phi0 shapes differ")
     nz, ny, nx = I.shape
     out = np.empty_like(phi0)
-    _lib(omp).rsf_oracle_evolve(_dp(I), _dp(phi0), _dp(out), nx, ny, nz, *_params(params), int(iters))
+    _lib(omp).rsf_oracle_evolve(_dp(I), _dp(phi0), _dp(out), nx, ny, nz, *_params(params), int(iters),
+                                _force(force))
     return out
 
 
 POINT_TERMS = ("e1", "e2", "g", "kappa", "lap")
 
 
-def point_next(I, phi, params: dict, x: int, y: int, z: int, terms: bool = False):
+def point_next(I, phi, params: dict, x: int, y: int, z: int, terms: bool = False, force: str = "li"):
     """phi_{n+1} at voxel (x, y, z) by direct triple sums (no separable passes).
 
     With ``terms``, returns (phi_next, {e1, e2, g, kappa, lap}) at the voxel."""
@@ -183,5 +196,5 @@ def point_next(I, phi, params: dict, x: int, y: int, z: int, terms: bool = False
     nz, ny, nx = I.shape
     t = np.zeros(len(POINT_TERMS), dtype=np.float64)
     v = float(_lib().rsf_oracle_point_next(_dp(I), _dp(phi), nx, ny, nz, int(x), int(y), int(z),
-                                           *_params(params), _dp(t) if terms else None))
+                                           *_params(params), _dp(t) if terms else None, _force(force)))
     return (v, dict(zip(POINT_TERMS, t.tolist()))) if terms else v

@@ -16,9 +16,13 @@
  *               exp(-k^2 / 2 sigma^2), k = -R..R, R = round(2 sigma),
  *               normalised to sum 1 (the printed normalisation is garbled)
  *   Eq. (8)-(10) H = H_eps(phi) = 1/2 (1 + 2/pi atan(phi/eps)), H_- = 1 - H
- *   Eq. (11)-(12) with Li et al.'s data terms:
+ *   Eq. (11)-(12) with Li et al.'s data terms (force mode 0):
  *               e_i = (K*1) I^2 - 2 I (K*f_i) + K*(f_i^2),
  *               F = -(lambda1 e_1 - lambda2 e_2)
+ *   Eq. (15)    the paper's own force with sigma_2 = 0, its setting for the
+ *               3-D runs (Sec. 5.3), force mode 1: K(sigma_2) is the
+ *               identity, so F_+- = I^2 - 2 r_+- I + r_+-^2 = (I - r_+-)^2
+ *               with r_+ = f_1, r_- = f_2; e_i = (I - f_i)^2 in the same F
  *   Eq. (3)-(4) kappa = div(grad phi / |grad phi|) (the printed operator is
  *               garbled; the curvature reading), L = 7-point Laplacian
  *   Eq. (14)    delta_eps(u) = (eps/pi) / (eps^2 + u^2)
@@ -195,10 +199,12 @@ int rsf_oracle_dump_slots(void) { return DUMP_NSLOTS; }
 
 /* One iteration given the precomputed K*1 (K1) and K*I (unused here: the
  * complement fit convolves (1-H) I directly) fields.  Writes phi_next. */
+enum { FORCE_LI = 0, FORCE_EQ15 = 1 };
+
 static void step_with(const double *I, const double *K1, const double *phi, double *phi_next,
                       i64 nx, i64 ny, i64 nz, double sigma, double eps,
                       double lambda1, double lambda2, double nu, double mu, double dt,
-                      double *dump)
+                      double *dump, int force)
 {
     i64 N = nx * ny * nz;
     double *H = (double *)malloc(sizeof(double) * N);
@@ -227,6 +233,15 @@ static void step_with(const double *I, const double *K1, const double *phi, doub
     rsf_oracle_conv3(d, c, nx, ny, nz, sigma);
     for (i64 p = 0; p < N; ++p) f2[p] = b[p] / c[p];
 
+    if (force == FORCE_EQ15) {
+        /* Eq. (15), sigma_2 = 0: e_i = (I - f_i)^2, g = l1 e1 - l2 e2 */
+        for (i64 p = 0; p < N; ++p) {
+            double e1 = (I[p] - f1[p]) * (I[p] - f1[p]);
+            double e2 = (I[p] - f2[p]) * (I[p] - f2[p]);
+            g[p] = lambda1 * e1 - lambda2 * e2;
+            if (dump) { dump[DUMP_E1 * N + p] = e1; dump[DUMP_E2 * N + p] = e2; }
+        }
+    } else {
     /* Eqs. (11)-(12): e_i = K1 I^2 - 2 I K*f_i + K*f_i^2, g = l1 e1 - l2 e2 */
     rsf_oracle_conv3(f1, a, nx, ny, nz, sigma);                  /* K*f1   */
     for (i64 p = 0; p < N; ++p) d[p] = f1[p] * f1[p];
@@ -243,6 +258,7 @@ static void step_with(const double *I, const double *K1, const double *phi, doub
         double e2 = K1[p] * I[p] * I[p] - 2.0 * I[p] * a[p] + b[p];
         g[p] -= lambda2 * e2;
         if (dump) dump[DUMP_E2 * N + p] = e2;
+    }
     }
 
     /* Eqs. (3)-(4) */
@@ -272,14 +288,14 @@ static void step_with(const double *I, const double *K1, const double *phi, doub
 void rsf_oracle_step(const double *I, const double *phi, double *phi_next,
                      i64 nx, i64 ny, i64 nz, double sigma, double eps,
                      double lambda1, double lambda2, double nu, double mu, double dt,
-                     double *dump)
+                     double *dump, int force)
 {
     i64 N = nx * ny * nz;
     double *one = (double *)malloc(sizeof(double) * N);
     double *K1 = (double *)malloc(sizeof(double) * N);
     for (i64 p = 0; p < N; ++p) one[p] = 1.0;
     rsf_oracle_conv3(one, K1, nx, ny, nz, sigma);
-    step_with(I, K1, phi, phi_next, nx, ny, nz, sigma, eps, lambda1, lambda2, nu, mu, dt, dump);
+    step_with(I, K1, phi, phi_next, nx, ny, nz, sigma, eps, lambda1, lambda2, nu, mu, dt, dump, force);
     free(one);
     free(K1);
 }
@@ -289,7 +305,7 @@ void rsf_oracle_step(const double *I, const double *phi, double *phi_next,
 void rsf_oracle_evolve(const double *I, const double *phi0, double *phi_out,
                        i64 nx, i64 ny, i64 nz, double sigma, double eps,
                        double lambda1, double lambda2, double nu, double mu, double dt,
-                       int iters)
+                       int iters, int force)
 {
     i64 N = nx * ny * nz;
     double *one = (double *)malloc(sizeof(double) * N);
@@ -300,7 +316,7 @@ void rsf_oracle_evolve(const double *I, const double *phi0, double *phi_out,
     rsf_oracle_conv3(one, K1, nx, ny, nz, sigma);
     memcpy(pa, phi0, sizeof(double) * N);
     for (int it = 0; it < iters; ++it) {
-        step_with(I, K1, pa, pb, nx, ny, nz, sigma, eps, lambda1, lambda2, nu, mu, dt, NULL);
+        step_with(I, K1, pa, pb, nx, ny, nz, sigma, eps, lambda1, lambda2, nu, mu, dt, NULL, force);
         double *t = pa; pa = pb; pb = t;
     }
     memcpy(phi_out, pa, sizeof(double) * N);
@@ -317,7 +333,7 @@ void rsf_oracle_evolve(const double *I, const double *phi0, double *phi_out,
 double rsf_oracle_point_next(const double *I, const double *phi, i64 nx, i64 ny, i64 nz,
                              i64 px, i64 py, i64 pz, double sigma, double eps,
                              double lambda1, double lambda2, double nu, double mu, double dt,
-                             double *terms)
+                             double *terms, int force)
 {
     double g[256];
     int R = rsf_oracle_taps(sigma, g);
@@ -333,7 +349,7 @@ double rsf_oracle_point_next(const double *I, const double *phi, i64 nx, i64 ny,
                 Hb[((c + 2 * R) * W + (b + 2 * R)) * W + (a + 2 * R)] = h;
             }
 
-    double K1 = 0.0, Kf1 = 0.0, Kf1s = 0.0, Kf2 = 0.0, Kf2s = 0.0;
+    double K1 = 0.0, Kf1 = 0.0, Kf1s = 0.0, Kf2 = 0.0, Kf2s = 0.0, f1p = 0.0, f2p = 0.0;
     for (int c = -R; c <= R; ++c)
         for (int b = -R; b <= R; ++b)
             for (int a = -R; a <= R; ++a) {
@@ -356,6 +372,7 @@ double rsf_oracle_point_next(const double *I, const double *phi, i64 nx, i64 ny,
                             d2 += ww * (1.0 - h);
                         }
                 double f1 = n1 / d1, f2 = n2 / d2;
+                if (a == 0 && b == 0 && c == 0) { f1p = f1; f2p = f2; }
                 K1 += w;
                 Kf1 += w * f1;
                 Kf1s += w * f1 * f1;
@@ -367,6 +384,10 @@ double rsf_oracle_point_next(const double *I, const double *phi, i64 nx, i64 ny,
     double Ip = I[idx3(px, py, pz, nx, ny)];
     double e1 = K1 * Ip * Ip - 2.0 * Ip * Kf1 + Kf1s;
     double e2 = K1 * Ip * Ip - 2.0 * Ip * Kf2 + Kf2s;
+    if (force == FORCE_EQ15) {          /* Eq. (15), sigma_2 = 0 */
+        e1 = (Ip - f1p) * (Ip - f1p);
+        e2 = (Ip - f2p) * (Ip - f2p);
+    }
     double gg = lambda1 * e1 - lambda2 * e2;
 
     /* unit normal at a (reflected) voxel, then its central-difference divergence */

@@ -23,6 +23,8 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 from typing import Optional, Tuple
 
+import os
+
 import numpy as np
 
 try:  # the point-spread blur and the box mean; scipy is present on both machines
@@ -154,13 +156,22 @@ def box_phi0(shape_zyx, box: int, c0: float = 2.0) -> np.ndarray:
     return phi
 
 
-def mean_rule_phi0(vol: np.ndarray, c0: float = 2.0) -> np.ndarray:
-    """+c0 where the 3x3x3 box mean of the image (clamped borders) exceeds the image mean."""
+def mean_rule_phi0(vol: np.ndarray, c0: float = 2.0, slab: int = 64) -> np.ndarray:
+    """+c0 where the 3x3x3 box mean of the image (clamped borders) exceeds the image mean.
+
+    Computed slab by slab along z (each slab with its neighbouring planes), so
+    that large volumes need no full-size float64 copy."""
     if _ndi is None:
         raise RuntimeError("scipy.ndimage is required for the box mean")
-    v = vol.astype(np.float64)
-    m = _ndi.uniform_filter(v, size=3, mode="nearest")
-    return np.where(m > v.mean(), c0, -c0).astype(np.float32)
+    nz = vol.shape[0]
+    mean = float(np.mean(vol, dtype=np.float64))
+    out = np.empty(vol.shape, dtype=np.float32)
+    for z0 in range(0, nz, slab):
+        z1 = min(z0 + slab, nz)
+        a, b = max(z0 - 1, 0), min(z1 + 1, nz)
+        m = _ndi.uniform_filter(vol[a:b].astype(np.float64), size=3, mode="nearest")[z0 - a:z0 - a + (z1 - z0)]
+        out[z0:z1] = np.where(m > mean, c0, -c0)
+    return out
 
 
 def tree_volume_u8(shape_zyx=(64, 64, 64), workload: int = 1, brick: int = 0, n_segments: int = 40,
@@ -267,6 +278,81 @@ def milling_volume_u8(shape_zyx, workload: int = 4, brick: int = 0, vessel_fract
     gain = 1.0 + stripe * np.sin(2.0 * np.pi * z / stripe_period)
     img = (bg + (fg - bg) * occ) * gain + rng.normal(0.0, noise, size=occ.shape)
     return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+
+
+@dataclass
+class MillingField:
+    """A uint8 milling-microscopy-like volume (dense capillary bed, radius 1-2
+    voxels, about 4 % vessel fraction, illumination striped by +-20 % along z
+    with period 64, Gaussian noise std 20), defined voxel by voxel so that any
+    box of it is rasterised on its own and equals that region of the whole:
+    segments are drawn once over the extent, occupancy is rasterised with a
+    margin for the point-spread blur, and noise is drawn per global z plane."""
+    extent_xyz: Tuple[int, int, int] = (1024, 1024, 1024)
+    workload: int = 4
+    vessel_fraction: float = 0.04
+    r_range: Tuple[float, float] = (1.0, 2.0)
+    fg: float = 200.0
+    bg: float = 30.0
+    stripe: float = 0.2
+    stripe_period: float = 64.0
+    noise: float = 20.0
+    psf: float = 1.0
+    seg: Segments = field(init=False)
+
+    def __post_init__(self):
+        ex, ey, ez = self.extent_xyz
+        mean_len, mean_r = 13.0, 0.5 * (self.r_range[0] + self.r_range[1])
+        n = max(4, int(self.vessel_fraction * ex * ey * ez / (np.pi * mean_r ** 2 * mean_len)))
+        self.seg = vessel_segments(rng_for(self.workload, 0), (ex, ey, ez), n, self.r_range)
+
+    def _plane_noise(self, z: int) -> np.ndarray:
+        rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([1000 * self.workload, 7, int(z)])))
+        ex, ey, _ = self.extent_xyz
+        return rng.normal(0.0, self.noise, size=(ey, ex))
+
+    def box(self, origin_xyz, shape_zyx) -> np.ndarray:
+        """uint8 [z, y, x] of the box at origin (x, y, z) with shape (nz, ny, nx)."""
+        m = int(np.ceil(3 * self.psf)) + 1
+        nz, ny, nx = (int(v) for v in shape_zyx)
+        ox, oy, oz = (int(v) for v in origin_xyz)
+        occ = rasterize(self.seg, (ox - m, oy - m, oz - m), (nz + 2 * m, ny + 2 * m, nx + 2 * m))
+        occ = _blur(occ, (self.psf,) * 3)[m:m + nz, m:m + ny, m:m + nx]
+        z = (oz + np.arange(nz, dtype=np.float64))[:, None, None]
+        img = (self.bg + (self.fg - self.bg) * occ) * (1.0 + self.stripe * np.sin(2.0 * np.pi * z / self.stripe_period))
+        for i in range(nz):
+            img[i] += self._plane_noise(oz + i)[oy:oy + ny, ox:ox + nx]
+        return np.clip(np.rint(img), 0, 255).astype(np.uint8)
+
+
+_FIELD_FOR_WORKER = None
+
+
+def _field_worker_init(f):
+    global _FIELD_FOR_WORKER
+    _FIELD_FOR_WORKER = f
+
+
+def _field_worker(job):
+    z0, nzs = job
+    ex, ey, _ = _FIELD_FOR_WORKER.extent_xyz
+    return z0, _FIELD_FOR_WORKER.box((0, 0, z0), (nzs, ey, ex))
+
+
+def field_volume(f: "MillingField", slab: int = 64, workers: Optional[int] = None) -> np.ndarray:
+    """The whole volume of a box-rasterised field, slabs of `slab` planes built by a
+    spawn-context process pool (safe after CUDA initialisation in the parent)."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+    ex, ey, ez = f.extent_xyz
+    jobs = [(z0, min(slab, ez - z0)) for z0 in range(0, ez, slab)]
+    workers = workers or max(1, min(16, os.cpu_count() or 1, len(jobs)))
+    if workers == 1:
+        return np.concatenate([f.box((0, 0, z0), (n, ey, ex)) for z0, n in jobs])
+    with ProcessPoolExecutor(max_workers=workers, mp_context=get_context("spawn"),
+                             initializer=_field_worker_init, initargs=(f,)) as pool:
+        parts = sorted(pool.map(_field_worker, jobs))
+    return np.concatenate([v for _, v in parts])
 
 
 @dataclass
