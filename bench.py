@@ -35,14 +35,16 @@ sys.path.insert(0, ROOT)
 # fields it must read once and write once, independent of tiling.  `img` is the
 # image's byte size (the tiled kernels read it in its own type), `st` the
 # storage byte size of the group-A fields and (a, b) (4, or 2 for FP16/BF16).
-def algo_bytes_per_voxel(img: int, st: int) -> dict:
+def algo_bytes_per_voxel(img: int, st: int, force: str = "li") -> dict:
+    # the Eq. (15) form writes (a, b) in FP32 from rsf_ta_z and has no rsf_tb_xy
+    ab_out = 8 if force == "eq15" else 2 * st
     return {
         # six-pass schedule (FP32 fields, centred FP32 image)
         "rsf_a_x": 4 + 4 + 16, "rsf_a_y": 16 + 16, "rsf_a_z": 16 + 8,
         "rsf_b_x": 8 + 8, "rsf_b_y": 8 + 8, "rsf_b_z": 8 + 4 + 4 + 4,
         # tiled schedule
         "rsf_ta_xy": 4 + img + 4 * st,          # q, I -> four group-A fields
-        "rsf_ta_z": 4 * st + 2 * st,            # four fields -> (a, b)
+        "rsf_ta_z": 4 * st + ab_out,            # four fields -> (a, b)
         "rsf_tb_xy": 2 * st + 8,                # (a, b) -> x/y-convolved (a, b), FP32
         "rsf_tb_z": 8 + img + 4 + 4 + 4,        # (a, b)_xy, I, phi -> phi', q(phi')
     }
@@ -50,6 +52,9 @@ def algo_bytes_per_voxel(img: int, st: int) -> dict:
 
 SETUP_LAUNCHES = 3  # statistics, their reduction, q of phi0
 NOMINAL_HBM_GBS = 7900.0
+# The paper's Table 1: one time step on a 500^3 volume takes 585 ms summed over
+# its kernels (Eq. (15) form, sigma_2 = 0), i.e. 1.25e8 / 0.585 s voxel-iterations/s.
+PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
@@ -152,6 +157,14 @@ def make_workload(name: str, rank: int, size=None, iters_override=None):
         vol = synth.field_volume(synth.MillingField(extent_xyz=(e, e, e), workload=4 + 100 * rank))
         params = synth.RSFParams().as_dict()
         return vol, synth.mean_rule_phi0(vol), params, iters_override or 300
+    if name == "paper500":
+        # the configuration of the paper's Table 1: a 500^3 volume, its 3-D parameter
+        # set (Sec. 5.3: sigma_1 = 5, sigma_2 = 0, dt = 0.06, alpha = 255^2 * 0.0009,
+        # beta = 0.1), on a uint8 milling-like (knife-edge scanning) vessel volume
+        e = size or 500
+        vol = synth.field_volume(synth.MillingField(extent_xyz=(e, e, e), workload=6 + 100 * rank))
+        params = dict(sigma=5.0, eps=1.0, lambda1=0.1, lambda2=0.1, nu=255.0 * 255.0 * 0.0009, mu=1.0, dt=0.06)
+        return vol, synth.mean_rule_phi0(vol), params, iters_override or 100
     if name == "lightsheet512":
         vol = synth.lightsheet_volume_u16((e, e, e), brick=rank)
         params = dict(sigma=3.0, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P_LIGHTSHEET ** 2, mu=1.0, dt=0.1)
@@ -411,7 +424,7 @@ def workload_desc(name, vol, params, iters):
             "l2": "inputs larger than L2 (each FP32 field 4*voxels bytes)"}
 
 
-def cpu_baseline_omp(vol, phi0, params, budget_s=10.0):
+def cpu_baseline_omp(vol, phi0, params, budget_s=10.0, force="li"):
     """The same oracle source built with OpenMP (loops over independent outputs split
     across all host cores, bit-identical results) on a bounded 128^3 crop."""
     import oracle
@@ -419,29 +432,29 @@ def cpu_baseline_omp(vol, phi0, params, budget_s=10.0):
     I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
     ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
     t0 = time.perf_counter()
-    oracle.evolve(I, ph, params, 1, omp=True)
+    oracle.evolve(I, ph, params, 1, omp=True, force=force)
     t1 = time.perf_counter() - t0
     its = max(1, min(20, int(budget_s / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    oracle.evolve(I, ph, params, its, omp=True)
+    oracle.evolve(I, ph, params, its, omp=True, force=force)
     dt = time.perf_counter() - t0
     return {"value": I.size * its / dt / 1e9, "unit": "GVoxel-iterations/s", "cores": os.cpu_count(),
             "kind": "oracle (OpenMP build)",
             "sample": f"{c}^3 corner crop of the workload volume, {its} iterations, FP64 C (-O2, OpenMP)"}
 
 
-def cpu_baseline(vol, phi0, params, budget_s=15.0):
+def cpu_baseline(vol, phi0, params, budget_s=15.0, force="li"):
     """The FP64 oracle (single thread) on a bounded corner crop of the same volume."""
     import oracle
     c = 64
     I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
     ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
     t0 = time.perf_counter()
-    oracle.evolve(I, ph, params, 1)
+    oracle.evolve(I, ph, params, 1, force=force)
     t1 = time.perf_counter() - t0
     its = max(1, min(40, int(budget_s / max(t1, 1e-3))))
     t0 = time.perf_counter()
-    oracle.evolve(I, ph, params, its)
+    oracle.evolve(I, ph, params, its, force=force)
     dt = time.perf_counter() - t0
     return {"value": I.size * its / dt / 1e9, "unit": "GVoxel-iterations/s", "cores": 1, "kind": "oracle",
             "sample": f"{c}^3 corner crop of the workload volume, {its} iterations, FP64 single-thread C (-O2)"}
@@ -457,16 +470,17 @@ def run_reference(args, rank, world):
         vol, phi0 = bricks[0]
     else:
         vol, phi0, params, iters = make_workload(args.workload, 0, args.size, args.iters)
+    force = args.force or ("eq15" if args.workload == "paper500" else "li")
     c = 48
     I = np.ascontiguousarray(vol[:c, :c, :c], dtype=np.float64)
     ph = np.ascontiguousarray(phi0[:c, :c, :c], dtype=np.float64)
     its = 4
     for _ in range(args.warmup):
-        oracle.evolve(I, ph, params, 1)
+        oracle.evolve(I, ph, params, 1, force=force)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.evolve(I, ph, params, its)
+        oracle.evolve(I, ph, params, its, force=force)
         times.append(time.perf_counter() - t0)
     T = sum(times)
     v = I.size * its * args.steps / T / 1e9
@@ -474,7 +488,7 @@ def run_reference(args, rank, world):
     out = {"impl": "reference", "metric": "GVoxel-iterations/s", "value": v, "unit": "GVoxel-iterations/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_desc(args.workload, vol, params, iters),
+           "config": dict(workload_desc(args.workload, vol, params, iters), force=force),
            "cpu_baseline": {"value": v, "unit": "GVoxel-iterations/s", "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": "GVoxel-iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -488,9 +502,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="rsf", choices=["rsf", "reference"])
     ap.add_argument("--workload", default="lightsheet512",
-                    choices=["lightsheet512", "lightsheet512_s5", "tree64", "milling1024", "bricks256", "serve"])
-    ap.add_argument("--requests", type=int, default=200, help="requests per arrival rate (serve)")
-    ap.add_argument("--rates", default="8,16,24,32", help="Poisson arrival rates in requests/s (serve)")
+                    choices=["lightsheet512", "lightsheet512_s5", "tree64", "milling1024", "paper500", "bricks256",
+                             "serve"])
+    ap.add_argument("--force", default=None, choices=["li", "eq15"],
+                    help="data-term form (default: eq15 for paper500, li otherwise)")
+    ap.add_argument("--requests", type=int, default=150, help="requests per arrival rate (serve)")
+    ap.add_argument("--rates", default="16,32,50,100,200,400", help="Poisson arrival rates in requests/s (serve)")
     ap.add_argument("--bricks", type=int, default=None, help="number of bricks of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -530,9 +547,11 @@ def main():
     v = torch.from_numpy(vol).cuda()
     ph0 = torch.from_numpy(phi0).cuda()
     out = torch.empty_like(ph0)
+    force = args.force or ("eq15" if args.workload == "paper500" else "li")
     ctx = rsf.Context(local)
     ctx.set_path(args.path)
     ctx.set_storage(args.storage)
+    ctx.set_force(force)
     stream = torch.cuda.ExternalStream(ctx.stream_handle)
 
     for _ in range(args.warmup):
@@ -584,36 +603,52 @@ def main():
     if args.workload == "milling1024" and args.storage != "f32":
         ctx.set_storage("f32")
         ref32 = ctx.evolve(v, ph0, params, iters)
+        # the map's own sensitivity: FP32 from phi0 moved by one ulp in a random direction per voxel
+        up = torch.from_numpy(np.random.default_rng(77).random(phi0.shape) < 0.5).cuda()
+        ph0p = torch.nextafter(ph0, torch.where(up, torch.full_like(ph0, float("inf")), torch.full_like(ph0, float("-inf"))))
+        ref32p = ctx.evolve(v, ph0p, params, iters)
         ctx.set_storage(args.storage)
-        a, b = out > 0, ref32 > 0
-        inter = float(torch.logical_and(a, b).sum().item())
-        vs_fp32 = {"sign_disagreement": float((a != b).float().mean().item()),
-                   "dice": 2.0 * inter / max(float(a.sum().item() + b.sum().item()), 1.0),
+        b = ref32 > 0
+
+        def agree(x):
+            a = x > 0
+            inter = float(torch.logical_and(a, b).sum().item())
+            return (float((a != b).float().mean().item()),
+                    2.0 * inter / max(float(a.sum().item() + b.sum().item()), 1.0))
+
+        dis, dice = agree(out)
+        env, env_dice = agree(ref32p)
+        vs_fp32 = {"sign_disagreement": dis, "dice": dice,
                    "max_abs_dphi": float((out - ref32).abs().max().item()),
-                   "note": f"{args.storage} storage vs FP32 storage, both on the GPU, after {iters} iterations"}
-        del ref32
+                   "fp32_self_envelope": {"sign_disagreement": env, "dice": env_dice},
+                   "note": f"{args.storage} storage vs FP32 storage, both on the GPU, after {iters} iterations; the "
+                           "envelope is FP32 against FP32 from a phi0 perturbed by one ulp per voxel"}
+        del ref32, ref32p, ph0p, up
 
     if rank == 0:
         peak, peak_kind = peaks()
         dom = max(prof, key=lambda k: prof[k][1])
         n_l, tot_ms = prof[dom]
         avg_s = tot_ms / max(n_l, 1) / 1e3
-        algo = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2)[dom] * n_vox
+        per_kernel = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2, force)
+        algo = per_kernel[dom] * n_vox
         achieved = algo / avg_s / 1e9
-        per_kernel = algo_bytes_per_voxel(vol.dtype.itemsize, 4 if args.storage == "f32" else 2)
         sched_bytes = sum(per_kernel[k] for k, (n, _) in prof.items() if n and k in per_kernel)
         tr = NCU_TRAFFIC.get(dom)
-        same_case = args.storage == "f32" and vol.dtype == np.uint16 and params["sigma"] == 3.0
+        same_case = args.storage == "f32" and vol.dtype == np.uint16 and params["sigma"] == 3.0 and force == "li"
         traffic = (tr["bytes_per_voxel"] * n_vox
                    if tr and same_case and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
         launches = SETUP_LAUNCHES * args.steps + sum(n for n, _ in prof.values())
         line = {
             "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": value / PAPER_TABLE1_GVOX_IT_S if args.workload == "paper500" and force == "eq15" else None,
             "dtype": "f32" if args.storage == "f32" else f"f32 compute, {args.storage} storage",
-            "data": "synthetic (seeded vessel-network volume, light-sheet-like)",
+            "data": "synthetic (seeded vessel-network volume, light-sheet-like)" if vol.dtype == np.uint16
+                    else "synthetic (seeded vessel-network volume, milling-like)",
             "config": dict(workload_desc(args.workload, vol, params, iters), storage=args.storage,
+                           force={"li": "li (e_i with K*1, K*f_i)", "eq15": "eq15 (paper's Eq. 15, sigma_2 = 0)"}[force],
                            parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -631,8 +666,8 @@ def main():
         if vs_fp32 is not None:
             line["vs_fp32"] = vs_fp32
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(vol, phi0, params)
-            line["cpu_baseline_omp"] = cpu_baseline_omp(vol, phi0, params)
+            line["cpu_baseline"] = cpu_baseline(vol, phi0, params, force=force)
+            line["cpu_baseline_omp"] = cpu_baseline_omp(vol, phi0, params, force=force)
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

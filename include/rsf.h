@@ -180,6 +180,16 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   k-th admission with RSF_E_CUDA, on the host, without any
  *                   device work (for testing failure handling); 0: off.  Read
  *                   when the serving loop starts (the first rsf_submit).
+ *   RSF_OPT_FORCE   the data terms e_1, e_2 of the force: RSF_FORCE_LI
+ *                   (default), Li et al.'s e_i = (K*1) I^2 - 2 I K*f_i +
+ *                   K*(f_i^2), read into Eqs. (11)-(12), which convolve the
+ *                   fits again (six convolved fields per iteration);
+ *                   RSF_FORCE_EQ15, the paper's own Eq. (15) with sigma_2 = 0,
+ *                   its setting for the 3-D runs (Sec. 5.3): e_i = (I - f_i)^2
+ *                   (four convolved fields).  RSF_FORCE_EQ15 needs the tiled
+ *                   path (RSF_E_INVAL otherwise).  rsf_evolve, rsf_step_stages
+ *                   and rsf_evolve_batch read it per call; rsf_submit per
+ *                   request.
  * The paths give the same result per voxel up to the order of FP32 rounding.
  * Errors: RSF_E_INVAL (unknown key or value).
  */
@@ -190,6 +200,9 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 #define RSF_OPT_GRAPH 5
 #define RSF_OPT_FAULT_ADMISSION 6
 #define RSF_OPT_SERVE_SLOTS 7
+#define RSF_OPT_FORCE 8
+#define RSF_FORCE_LI 0
+#define RSF_FORCE_EQ15 1
 #define RSF_PATH_AUTO 0
 #define RSF_PATH_PASSES 1
 #define RSF_PATH_TILED 2

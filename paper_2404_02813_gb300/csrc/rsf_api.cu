@@ -151,6 +151,7 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
         const int nb = (int)gs.bricks.size();
         rsf::TiledGroup g{};
         g.storage = gs.storage;
+        g.force = gs.force;
         g.imgtype = gs.imgtype;
         g.taps = gs.taps;
         g.bricks = buf.d_bricks + all.size();
@@ -394,13 +395,17 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         return fail(RSF_E_INVAL, "the tiled path has no kernels for radius %d", taps.R);
     if (storage != RSF_STORE_F32 && !tiled)
         return fail(RSF_E_INVAL, "16-bit storage needs the tiled path (radius %d, path option %d)", taps.R, c->opt_path);
+    const int force = c->opt_force;
+    if (force != RSF_FORCE_LI && !tiled)
+        return fail(RSF_E_INVAL, "the Eq. (15) force form needs the tiled path (radius %d, path option %d)", taps.R,
+                    c->opt_path);
     // the tiled path reads the image in its own type and centres it on load
     RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream, !tiled));
     RSF_CUDA(cudaMemcpyAsync(f.phi[0], phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
     RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
     int cur = 0;
     if (tiled) {
-        RSF_CUDA(rsf::tiled_prepare(storage, taps.R));
+        RSF_CUDA(rsf::tiled_prepare(storage, taps.R, force));
         rsf::BrickDev b{};
         b.nx = (int)nx;
         b.ny = (int)ny;
@@ -431,6 +436,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         b.dump = dump;  // only rsf_step_stages asks for stages, and it runs one iteration
         std::vector<GroupSpec> specs(1);
         specs[0].storage = storage;
+        specs[0].force = force;
         specs[0].imgtype = (int)vt;
         specs[0].taps = taps;
         specs[0].bricks.push_back(b);
@@ -498,6 +504,11 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
             if (value != RSF_STORE_F32 && value != RSF_STORE_BF16 && value != RSF_STORE_F16)
                 return fail(RSF_E_INVAL, "unknown storage %lld", (long long)value);
             c->opt_storage = (int)value;
+            return RSF_OK;
+        case RSF_OPT_FORCE:
+            if (value != RSF_FORCE_LI && value != RSF_FORCE_EQ15)
+                return fail(RSF_E_INVAL, "unknown force form %lld", (long long)value);
+            c->opt_force = (int)value;
             return RSF_OK;
         case RSF_OPT_SERVE_SLOTS:
             if (value < 1 || value > (1 << 20)) return fail(RSF_E_INVAL, "slots must lie in [1, 2^20]");

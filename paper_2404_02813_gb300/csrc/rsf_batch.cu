@@ -65,7 +65,7 @@ std::string group_key(const GroupSpec &g) {
     long long vox = 0;
     for (const rsf::BrickDev &b : g.bricks) vox += (long long)b.nx * b.ny * b.nz;
     char buf[128];
-    snprintf(buf, sizeof buf, "R%d/i%d/s%d/nb%zu/v%lld", g.taps.R, g.imgtype, g.storage, g.bricks.size(),
+    snprintf(buf, sizeof buf, "R%d/i%d/s%d/f%d/nb%zu/v%lld", g.taps.R, g.imgtype, g.storage, g.force, g.bricks.size(),
              (long long)std::llround(std::log2((double)std::max(vox, 1LL))));
     return buf;
 }
@@ -145,6 +145,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
     std::lock_guard<std::mutex> lk(c->mu);
     RSF_CUDA(cudaSetDevice(c->device));
     const int storage = c->opt_storage;
+    const int force = c->opt_force;
     int sms = 0;
     RSF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
 
@@ -256,13 +257,14 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
                 keys.push_back(k);
                 specs.emplace_back();
                 specs.back().storage = storage;
+                specs.back().force = force;
                 specs.back().imgtype = (int)bs[i].vt;
                 specs.back().taps = tp;
             }
             specs[gi].bricks.push_back(bs[i].d);
         }
         for (GroupSpec &g : specs) {
-            RSF_CUDA(rsf::tiled_prepare(storage, g.taps.R));
+            RSF_CUDA(rsf::tiled_prepare(storage, g.taps.R, force));
             if (c->opt_zchunk > 0) {
                 set_zc(g, c->opt_zchunk);
             } else if (c->opt_autotune && t == 0 && !tuned_once) {

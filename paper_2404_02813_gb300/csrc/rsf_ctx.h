@@ -40,6 +40,7 @@ struct rsf_ctx {
     int opt_path = RSF_PATH_AUTO;
     int opt_zchunk = 0;
     int opt_storage = RSF_STORE_F32;
+    int opt_force = RSF_FORCE_LI;
     DescBuffers desc;                   // brick descriptors of rsf_evolve / rsf_evolve_batch launches
     int opt_autotune = 0;
     int opt_graph = 1;
@@ -55,7 +56,7 @@ struct rsf_ctx {
 
 // One launch group before upload: bricks sharing radius, image type, storage.
 struct GroupSpec {
-    int storage = 0, imgtype = 0;
+    int storage = 0, imgtype = 0, force = 0;
     rsf::Taps taps{};
     std::vector<rsf::BrickDev> bricks;
 };

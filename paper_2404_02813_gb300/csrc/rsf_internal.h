@@ -108,6 +108,7 @@ struct BrickDev {
 // A set of bricks launched together: same radius, image type and storage.
 struct TiledGroup {
     int storage;            // 0 FP32, 1 BF16, 2 FP16 (rsf_storage)
+    int force;              // 0 Li's data terms (group B convolutions), 1 Eq. (15) with sigma_2 = 0
     int imgtype;            // 0 uint8, 1 uint16, 2 float
     Taps taps;
     const BrickDev *bricks; // device array of nb descriptors
@@ -119,7 +120,7 @@ struct TiledGroup {
 // Tiled four-kernel path (rsf_tiled*.cu) for the radii it is instantiated for.
 bool tiled_supports(int R);
 int tiled_pitch(int nx);
-cudaError_t tiled_prepare(int storage, int R);
+cudaError_t tiled_prepare(int storage, int R, int force);
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
 void tiled_cta_counts(const BrickDev &b, unsigned counts[4]);
 size_t tiled_stage_bytes(int storage, long long np);

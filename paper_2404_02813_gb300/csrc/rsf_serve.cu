@@ -8,7 +8,7 @@
 // ordered pool, its image statistics, K*1 profiles, phi0 and q are prepared on
 // a set-up stream, and the compute stream waits on that work.  A tick is one
 // iteration of every active brick -- one launch per kernel for each group of
-// bricks sharing a kernel radius, image type and storage (the batched kernels
+// bricks sharing a kernel radius, image type, storage and force form (the batched kernels
 // of rsf_evolve_batch); a brick admitted at tick T0 runs its iteration k at
 // tick T0 + k (its buffer parity is flipped accordingly).  A brick that has
 // done its iterations (or was cancelled) retires at once: its phi is copied to
@@ -65,7 +65,7 @@ struct Request {
     // set at admission
     rsf::BrickDev d{};
     rsf::Taps taps{};
-    int imgtype = 0, storage = 0;
+    int imgtype = 0, storage = 0, force = 0;
     long long n = 0;
     size_t bytes = 0;
     void *mem = nullptr;
@@ -246,7 +246,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
         return fail_admit(RSF_E_CUDA);
     if (q.iters > 0 && rsf::tiled_q_init(d.phi[0], d.q[0], n, q.eps, s->s_setup) != cudaSuccess)
         return fail_admit(RSF_E_CUDA);
-    if (rsf::tiled_prepare(r->storage, r->taps.R) != cudaSuccess) return fail_admit(RSF_E_CUDA);
+    if (rsf::tiled_prepare(r->storage, r->taps.R, r->force) != cudaSuccess) return fail_admit(RSF_E_CUDA);
     if (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess) return fail_admit(RSF_E_CUDA);
     cudaEventRecord(r->ready, s->s_setup);
     if (cudaGetLastError() != cudaSuccess) return fail_admit(RSF_E_CUDA);
@@ -276,14 +276,15 @@ void rebuild_groups(Server *s) {
     std::vector<std::shared_ptr<Request>> order = s->active;
     std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a->n > b->n; });
     std::vector<GroupSpec> specs;
-    std::vector<std::tuple<int, int, int>> keys;
+    std::vector<std::tuple<int, int, int, int>> keys;
     for (const auto &r : order) {
-        std::tuple<int, int, int> k{r->taps.R, r->imgtype, r->storage};
+        std::tuple<int, int, int, int> k{r->taps.R, r->imgtype, r->storage, r->force};
         size_t gi = std::find(keys.begin(), keys.end(), k) - keys.begin();
         if (gi == keys.size()) {
             keys.push_back(k);
             specs.emplace_back();
             specs.back().storage = r->storage;
+            specs.back().force = r->force;
             specs.back().imgtype = r->imgtype;
             specs.back().taps = r->taps;
         }
@@ -462,6 +463,7 @@ extern "C" rsf_status rsf_submit(rsf_ctx *c, const rsf_request *req, uint64_t *t
     if (!s) return st;
     auto r = std::make_shared<Request>();
     r->req = *req;
+    r->force = c->opt_force;  // the context's data-term form at submission
     r->t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(s->mu);

@@ -135,6 +135,8 @@ struct GroupArgs {
     const int *starts;  // nb + 1 CTA offsets of this kernel within the launch
     int nb;
     int parity;         // launch parity: a brick reads phi[p], q[p] with p = parity ^ flip, writes the other
+    int ab_f32;         // 1: rsf_ta_z writes (a, b) in FP32 to abxy, where the update kernel of the
+                        // Eq. (15) form reads them without group-B convolutions
 };
 
 // ---------------------------------------------------------------- x / y
@@ -492,7 +494,9 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
 #pragma unroll
             for (int j = 0; j < WIN; ++j) w[j] = az_read<R, S>(buf, 1, (zb + j) * 32 + lane);
             const long long pplane = (long long)B.px * B.ny;
-            V2 *ab = reinterpret_cast<V2 *>(B.ab) + (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
+            const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
+            V2 *ab = reinterpret_cast<V2 *>(B.ab) + off;
+            float2 *abf = B.abxy + off;
             float *const dump = B.dump;
 #pragma unroll
             for (int o = 0; o < kAZO; ++o) {
@@ -502,8 +506,11 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
 #pragma unroll
                     for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
                     const float f2 = __fdividef(acc.x, acc.y);
-                    ab[o * pplane] =
-                        Store<S>::pack2(make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2)));
+                    const float2 v = make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2));
+                    if (G.ab_f32)
+                        abf[o * pplane] = v;
+                    else
+                        ab[o * pplane] = Store<S>::pack2(v);
                     if (dump) {
                         const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
                         const long long n = (long long)B.nx * B.ny * B.nz;
@@ -562,7 +569,7 @@ __device__ __forceinline__ float heaviside_q_fast(float u, float eps) {
 // normal of plane -1 is that of plane 1 and the normal of plane nz that of
 // plane nz-2 (the prologue and the step loop copy them).
 template <int R>
-constexpr int tbz_ring() { return 2 * R + 4 <= 16 ? 16 : 32; }
+constexpr int tbz_ring() { return 2 * R + 4 <= 4 ? 4 : (2 * R + 4 <= 8 ? 8 : (2 * R + 4 <= 16 ? 16 : 32)); }
 
 constexpr int kZPhiRing = 16, kZNrmRing = 8;
 constexpr int kZPW = kZX + 4, kZPH = kZY + 4;  // phi tile, halo 2
@@ -575,7 +582,8 @@ template <int R, class ImgT>
 __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G, TapPairs t) {
     constexpr int T = 2 * R + 1;
     constexpr int M = tbz_ring<R>();
-    constexpr int SPB = M / 2;  // steps per unrolled body
+    constexpr int SPB = (M < kZPhiRing ? kZPhiRing : M) / 2;  // steps per unrolled body: 2 SPB planes, a multiple
+                                                              // of the phi, normal and (a, b) ring sizes
     constexpr int PW = kZPW, PH = kZPH, NW = kZNW, NH = kZNH;
     constexpr int PPL = PH * PW, NPL = 3 * NH * NW;
     constexpr int NPE = (PH * PW + kZThreads - 1) / kZThreads;
@@ -683,7 +691,9 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     fetch_phi(z0 + 4, pva);
     fetch_phi(z0 + 5, pvb);
 
-    const float pxy = active ? __ldg(B.prof + x) * __ldg(B.prof + nx + y) : 0.f;
+    // K*1 = p_x p_y p_z; with R = 0 (the Eq. (15) form, sigma_2 = 0) the data terms
+    // take no convolution and K*1 is 1
+    const float pxy = R == 0 ? 1.f : (active ? __ldg(B.prof + x) * __ldg(B.prof + nx + y) : 0.f);
     const float *profz = B.prof + nx + ny + z0;
     const float l12 = B.lambda1 - B.lambda2, s2 = B.cs[2];
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
@@ -741,7 +751,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
 #pragma unroll
                         for (int kt = 0; kt < T; ++kt) acc = f2fma(t.g[kt], ring[(2 * kk + c + kt) % M], acc);
                         const float im = c ? im1 : im0;
-                        const float K1 = pxy * __ldg(profz + r0 + c);
+                        const float K1 = R == 0 ? 1.f : pxy * __ldg(profz + r0 + c);
                         const float g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
                         const float *p0 = phi_at(2 * kk + c);
                         const int pc0 = (ty + 2) * PW + tx + 2;
@@ -808,7 +818,7 @@ cudaError_t prepare_storage() {
 
 template <int R, class S>
 cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, nullptr, g.nb, parity};
+    GroupArgs G{g.bricks, nullptr, g.nb, parity, g.force};
     const TapPairs tp = tap_pairs(g.taps);
     {
         ProfScope ps(prof, KID_TA_XY);
@@ -826,7 +836,7 @@ cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cuda
         const unsigned grid = g.ncta[1] < (unsigned)az_persist<R, S>() ? g.ncta[1] : (unsigned)az_persist<R, S>();
         k_ta_z<R, S><<<grid, kAZThreads, az_smem<R, S>(), s>>>(G, tp);
     }
-    {
+    if (!g.force) {  // the Eq. (15) form has no group-B convolutions
         ProfScope ps(prof, KID_TB_XY);
         G.starts = g.starts[2];
         constexpr size_t sm = XYLayout<R, 1>::bytes;

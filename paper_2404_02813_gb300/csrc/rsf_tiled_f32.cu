@@ -9,9 +9,14 @@ namespace tiled {
 namespace {
 template <int R, class ImgT>
 cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, g.starts[3], g.nb, parity};
+    GroupArgs G{g.bricks, g.starts[3], g.nb, parity, 0};
     ProfScope ps(prof, KID_TB_Z);
-    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem(), s>>>(G, tap_pairs(g.taps));
+    Taps t = g.taps;
+    if (R == 0) {  // the Eq. (15) form: one unit tap, no convolution of (a, b)
+        t.R = 0;
+        t.g[0] = 1.f;
+    }
+    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem(), s>>>(G, tap_pairs(t));
     return cudaGetLastError();
 }
 template <int R>
@@ -39,6 +44,7 @@ __global__ void k_q_init(const float *__restrict__ phi, float *__restrict__ q, l
 
 cudaError_t prepare_tb_z(int R) {
     switch (R) {
+        case 0: return prepare_bz_i<0>();
         case 2: return prepare_bz_i<2>();
         case 3: return prepare_bz_i<3>();
         case 4: return prepare_bz_i<4>();
@@ -52,7 +58,8 @@ cudaError_t prepare_tb_z(int R) {
 }
 
 cudaError_t launch_tb_z(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    switch (g.taps.R) {
+    switch (g.force ? 0 : g.taps.R) {
+        case 0: return launch_bz_i<0>(g, parity, prof, s);
         case 2: return launch_bz_i<2>(g, parity, prof, s);
         case 3: return launch_bz_i<3>(g, parity, prof, s);
         case 4: return launch_bz_i<4>(g, parity, prof, s);
@@ -86,8 +93,8 @@ cudaError_t tiled_launch_bf16(const TiledGroup &g, int parity, Profiler *prof, c
 cudaError_t tiled_prepare_f16(int R);
 cudaError_t tiled_prepare_bf16(int R);
 
-cudaError_t tiled_prepare(int storage, int R) {
-    const cudaError_t e = tiled::prepare_tb_z(R);
+cudaError_t tiled_prepare(int storage, int R, int force) {
+    const cudaError_t e = tiled::prepare_tb_z(force ? 0 : R);
     if (e != cudaSuccess) return e;
     switch (storage) {
         case 0: return tiled::prepare_group_s<float>(R);

@@ -30,8 +30,11 @@ EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_s
             "rsf_serve_stats")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
+OPT_FORCE = 8
 PATHS = {"auto": 0, "passes": 1, "tiled": 2}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+# data-term forms: Li et al.'s (default) and the paper's Eq. (15) with sigma_2 = 0
+FORCES = {"li": 0, "eq15": 1}
 
 NOALLOC_MAX_VOXELS = 1 << 18
 
@@ -303,6 +306,10 @@ class Context:
     def set_storage(self, name: str):
         """Storage of the intermediate fields: 'f32', 'bf16' or 'f16'."""
         self.set_option(OPT_STORAGE, STORAGE[name])
+
+    def set_force(self, name: str):
+        """Data-term form: 'li' (default) or 'eq15' (the paper's Eq. (15), sigma_2 = 0)."""
+        self.set_option(OPT_FORCE, FORCES[name])
 
     # kernel timing ---------------------------------------------------------
     def prof_enable(self, on: bool = True):

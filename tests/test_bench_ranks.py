@@ -35,7 +35,8 @@ def _rank_main(rank, world, port, q):
         vol, phi0, _, _ = bench.make_workload("lightsheet512", rank, size=24, iters_override=2)
         digest = float(np.asarray(vol, dtype=np.float64).sum())
         # the reference arm: rank 0 prints one line, the others nothing
-        args = type("A", (), dict(workload="tree64", bricks=None, size=None, iters=None, warmup=0, steps=1))()
+        args = type("A", (), dict(workload="tree64", bricks=None, size=None, iters=None, warmup=0, steps=1,
+                                  force=None))()
         buf = io.StringIO()
         with contextlib.redirect_stdout(buf):
             bench.run_reference(args, rank, world)
