@@ -198,3 +198,62 @@ def point_next(I, phi, params: dict, x: int, y: int, z: int, terms: bool = False
     v = float(_lib().rsf_oracle_point_next(_dp(I), _dp(phi), nx, ny, nz, int(x), int(y), int(z),
                                            *_params(params), _dp(t) if terms else None, _force(force)))
     return (v, dict(zip(POINT_TERMS, t.tolist()))) if terms else v
+
+
+# ------------------------------------------------ volume-level curtain scheme
+#
+# Sec. 4.1: a large volume is divided into sub-volumes processed independently,
+# overlapping by a curtain region, and neighbouring results are merged by linear
+# interpolation across the curtain.  Reading (the paper gives no formula):
+#   * along each axis of length n, sub-volumes of `edge` voxels start at
+#     multiples of edge - curtain; the last one is moved to end at n (one
+#     sub-volume when edge >= n); neighbours overlap by at least `curtain`;
+#   * sub-volume b has the weight w_b(x) = prod over axes of h_b(x_a), with
+#     h = 1 inside, rising linearly over the `curtain` voxels after each face
+#     interior to the volume: h = min(1, (x - s + 1/2)/curtain) after a start
+#     face s > 0 and min(1, (e - x - 1/2)/curtain) before an end face e < n;
+#   * the merged phi is sum_b w_b phi_b / sum_b w_b, which is the linear
+#     interpolation across an overlap of exactly `curtain` voxels.
+# Every sub-volume is evolved as its own volume (its own zero padding and
+# reflect-101 faces).
+
+def curtain_starts(n: int, edge: int, curtain: int) -> list:
+    if edge >= n:
+        return [0]
+    step = edge - curtain
+    starts = list(range(0, n - edge, step))
+    return starts + [n - edge]
+
+
+def curtain_weight(x: np.ndarray, s: int, e: int, n: int, curtain: int) -> np.ndarray:
+    h = np.ones(x.shape, dtype=np.float64)
+    if s > 0:
+        h = np.minimum(h, (x - s + 0.5) / curtain)
+    if e < n:
+        h = np.minimum(h, (e - x - 0.5) / curtain)
+    return np.clip(h, 0.0, 1.0)
+
+
+def curtain_evolve(I, phi0, params: dict, iters: int, edge: int, curtain: int, omp: bool = False,
+                   force: str = "li") -> np.ndarray:
+    """The curtain scheme: every sub-volume evolved by `evolve`, then merged."""
+    I = _vol(I)
+    phi0 = _vol(phi0)
+    nz, ny, nx = I.shape
+    num = np.zeros(I.shape, dtype=np.float64)
+    den = np.zeros(I.shape, dtype=np.float64)
+    for z0 in curtain_starts(nz, edge, curtain):
+        z1 = min(z0 + edge, nz)
+        wz = curtain_weight(np.arange(z0, z1, dtype=np.float64), z0, z1, nz, curtain)
+        for y0 in curtain_starts(ny, edge, curtain):
+            y1 = min(y0 + edge, ny)
+            wy = curtain_weight(np.arange(y0, y1, dtype=np.float64), y0, y1, ny, curtain)
+            for x0 in curtain_starts(nx, edge, curtain):
+                x1 = min(x0 + edge, nx)
+                wx = curtain_weight(np.arange(x0, x1, dtype=np.float64), x0, x1, nx, curtain)
+                sub = evolve(I[z0:z1, y0:y1, x0:x1], phi0[z0:z1, y0:y1, x0:x1], params, iters, omp=omp,
+                             force=force)
+                w = wz[:, None, None] * wy[None, :, None] * wx[None, None, :]
+                num[z0:z1, y0:y1, x0:x1] += w * sub
+                den[z0:z1, y0:y1, x0:x1] += w
+    return num / den
