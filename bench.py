@@ -81,6 +81,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def _curtain_starts(n: int, edge: int, width: int) -> list:
+    """Sub-volume starts of the curtain scheme along one axis (the layout rsf_evolve_curtain
+    documents), for counting the voxels the sub-volumes process."""
+    if edge >= n:
+        return [0]
+    return list(range(0, n - edge, edge - width)) + [n - edge]
+
+
 def max_over_ranks(x: float, world: int, device="cuda") -> float:
     """The largest of each rank's `x` (the slowest rank's time); `x` itself at N = 1."""
     if world == 1:
@@ -504,6 +512,9 @@ def main():
     ap.add_argument("--workload", default="lightsheet512",
                     choices=["lightsheet512", "lightsheet512_s5", "tree64", "milling1024", "paper500", "bricks256",
                              "serve"])
+    ap.add_argument("--curtain", type=int, default=None,
+                    help="evolve through the curtain scheme with sub-volumes of this edge (Sec. 4.1)")
+    ap.add_argument("--curtain-width", type=int, default=None, help="curtain width (default round(3 sigma))")
     ap.add_argument("--force", default=None, choices=["li", "eq15"],
                     help="data-term form (default: eq15 for paper500, li otherwise)")
     ap.add_argument("--requests", type=int, default=150, help="requests per arrival rate (serve)")
@@ -554,8 +565,22 @@ def main():
     ctx.set_force(force)
     stream = torch.cuda.ExternalStream(ctx.stream_handle)
 
+    # one step: rsf_evolve, or the curtain scheme over sub-volumes (Sec. 4.1)
+    nbox, sub_vox, width = 1, n_vox, None
+    if args.curtain:
+        width = args.curtain_width or int(np.floor(3 * params["sigma"] + 0.5))
+        boxes = [_curtain_starts(nn, args.curtain, width) for nn in vol.shape]
+        nbox = int(np.prod([len(b) for b in boxes]))
+        sub_vox = nbox * int(np.prod([min(args.curtain, nn) for nn in vol.shape]))
+
+        def step(a, b, o):
+            ctx.evolve_curtain(a, b, params, iters, args.curtain, width, out=o)
+    else:
+        def step(a, b, o):
+            ctx.evolve(a, b, params, iters, out=o)
+
     for _ in range(args.warmup):
-        ctx.evolve(v, ph0, params, iters, out=out)
+        step(v, ph0, out)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
@@ -567,7 +592,7 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        ctx.evolve(v, ph0, params, iters, out=out)
+        step(v, ph0, out)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -586,12 +611,12 @@ def main():
         vh = torch.from_numpy(vol).pin_memory()
         ph = torch.from_numpy(phi0).pin_memory()
         oh = torch.empty_like(ph).pin_memory()
-        ctx.evolve(vh, ph, params, iters, out=oh)
+        step(vh, ph, oh)
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ctx.evolve(vh, ph, params, iters, out=oh)
+            step(vh, ph, oh)
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world)
         e2e = {"value": whole_job_rate(rank_vox_it, world, te), "unit": "GVoxel-iterations/s",
@@ -638,7 +663,8 @@ def main():
         same_case = args.storage == "f32" and vol.dtype == np.uint16 and params["sigma"] == 3.0 and force == "li"
         traffic = (tr["bytes_per_voxel"] * n_vox
                    if tr and same_case and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
-        launches = SETUP_LAUNCHES * args.steps + sum(n for n, _ in prof.values())
+        launches = sum(n for n, _ in prof.values()) + (SETUP_LAUNCHES * args.steps if not args.curtain
+                                                       else (5 * nbox + 1) * args.steps)
         line = {
             "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -648,6 +674,9 @@ def main():
             "data": "synthetic (seeded vessel-network volume, light-sheet-like)" if vol.dtype == np.uint16
                     else "synthetic (seeded vessel-network volume, milling-like)",
             "config": dict(workload_desc(args.workload, vol, params, iters), storage=args.storage,
+                           **({"curtain": {"edge": args.curtain, "width": width, "subvolumes": nbox,
+                                           "subvolume_gvox_it_s": value * sub_vox / n_vox}}
+                              if args.curtain else {}),
                            force={"li": "li (e_i with K*1, K*f_i)", "eq15": "eq15 (paper's Eq. 15, sigma_2 = 0)"}[force],
                            parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

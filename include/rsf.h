@@ -130,6 +130,32 @@ typedef struct {
 rsf_status rsf_evolve_batch(rsf_ctx *ctx, const rsf_brick *bricks, int32_t nbricks);
 
 /*
+ * rsf_evolve_curtain -- the volume-level parallelism of Sec. 4.1: the volume
+ * is divided into overlapping sub-volumes, each is evolved as a volume of its
+ * own (all together, as by rsf_evolve_batch), and neighbouring results are
+ * merged by linear interpolation across the overlap (the curtain).
+ *   Along each axis of length n, sub-volumes of `edge` voxels start at
+ *   multiples of edge - curtain and the last one is moved to end at n (one
+ *   sub-volume when edge >= n); neighbours overlap by at least `curtain`.
+ *   Sub-volume b has the weight w_b(x) = product over the axes of h, with
+ *   h = 1 inside, min(1, (x - s + 1/2)/curtain) after a start face s > 0 and
+ *   min(1, (e - x - 1/2)/curtain) before an end face e < n; the result is
+ *   sum_b w_b phi_b / sum_b w_b (FP32).
+ *   edge      sub-volume edge in voxels, >= 4.
+ *   curtain   overlap in voxels, 1 <= curtain <= edge / 2.
+ * The other arguments are those of rsf_evolve (host or device pointers;
+ * phi_out may alias phi0).  The context's storage and force options apply;
+ * round(2 sigma) must be a radius with tiled kernels.  Blocking.  Device
+ * memory: every sub-volume's image and phi, staging of host inputs, plus
+ * what rsf_evolve_batch takes.
+ * Errors: RSF_E_INVAL (arguments), RSF_E_NOMEM, RSF_E_CUDA.
+ */
+rsf_status rsf_evolve_curtain(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                              const float *phi0, float *phi_out, float sigma, float eps, float lambda1,
+                              float lambda2, float nu, float mu, float dt, int32_t iters, int32_t edge,
+                              int32_t curtain);
+
+/*
  * rsf_step_stages -- one iteration from phi with the intermediate fields
  * written out, for checking each stage against a reference.
  *   stages   host or device buffer of RSF_NSTAGES * nx*ny*nz floats,

@@ -27,7 +27,7 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
-            "rsf_serve_stats")
+            "rsf_serve_stats", "rsf_evolve_curtain")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_evolve_noalloc.restype = i32
     L.rsf_evolve_batch.argtypes = [vp, ctypes.POINTER(Brick), i32]
     L.rsf_evolve_batch.restype = i32
+    L.rsf_evolve_curtain.argtypes = [vp, vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, i32, i32]
+    L.rsf_evolve_curtain.restype = i32
     L.rsf_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.rsf_submit.restype = i32
     L.rsf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
@@ -228,6 +230,20 @@ class Context:
         _order_after_caller(volume, phi0, out)
         _check(load_library().rsf_evolve(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0),
                                          _ptr(out), *p.tuple(), int(iters)))
+        return out
+
+    def evolve_curtain(self, volume, phi0, params, iters: int, edge: int, curtain: int, out=None):
+        """rsf_evolve_curtain: overlapping sub-volumes of `edge` voxels evolved together and
+        merged by linear interpolation across `curtain` voxels; returns `out`."""
+        p = Params.of(params)
+        nz, ny, nx = _shape(volume)
+        if _shape(phi0) != (nz, ny, nx):
+            raise ValueError("volume and phi0 shapes differ")
+        if out is None:
+            out = phi0.clone() if hasattr(phi0, "clone") else np.empty_like(phi0)
+        _order_after_caller(volume, phi0, out)
+        _check(load_library().rsf_evolve_curtain(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0),
+                                                 _ptr(out), *p.tuple(), int(iters), int(edge), int(curtain)))
         return out
 
     def step_stages(self, volume, phi, params, phi_next=None, stages=None):
