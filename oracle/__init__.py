@@ -257,3 +257,80 @@ def curtain_evolve(I, phi0, params: dict, iters: int, edge: int, curtain: int, o
                 num[z0:z1, y0:y1, x0:x1] += w * sub
                 den[z0:z1, y0:y1, x0:x1] += w
     return num / den
+
+
+# ---------------------------------------------------- initialisation (Sec. 4.3)
+#
+# Seeds: per z slice, determinant-of-Hessian blob detection.  Reading (the paper
+# names the detector, not its discretisation):
+#   * taps of the sampled Gaussian and of its first and second derivatives,
+#     k = -R..R with R = round(3 sigma): g_k = exp(-k^2/2s^2) / sum_j exp(-j^2/2s^2),
+#     g'_k = -(k/s^2) g_k, g''_k = (k^2/s^4 - 1/s^2) g_k;
+#   * in-slice filtering by correlation with zero padding:
+#     I_xx = (g'' along x, g along y), I_yy = (g along x, g'' along y),
+#     I_xy = (g' along x, g' along y);
+#   * D = s^4 (I_xx I_yy - I_xy^2) (scale-normalised), kept where
+#     I_xx + I_yy < 0 (bright blobs), else -inf;
+#   * a voxel is a seed when D > t * max of D over its slice (t the relative
+#     threshold, the maximum positive) and D exceeds D at each of its in-slice
+#     neighbours (the 8 that exist).
+# phi0 = r0 - d, d the Euclidean distance to the nearest seed (the distance
+# the paper's fast sweeping approximates; here exact).
+
+def deriv_taps(s: float):
+    R = int(np.floor(3.0 * s + 0.5))
+    k = np.arange(-R, R + 1, dtype=np.float64)
+    g = np.exp(-k * k / (2.0 * s * s))
+    g /= g.sum()
+    return k, g, -(k / (s * s)) * g, (k * k / s ** 4 - 1.0 / (s * s)) * g
+
+
+def _corr_axis(F: np.ndarray, w: np.ndarray, axis: int) -> np.ndarray:
+    """out(i) = sum_k w_k F(i + k) along `axis`, zero outside."""
+    R = (w.size - 1) // 2
+    pad = [(0, 0)] * F.ndim
+    pad[axis] = (R, R)
+    P = np.pad(F, pad)
+    out = np.zeros_like(F)
+    n = F.shape[axis]
+    for j in range(w.size):
+        sl = [slice(None)] * F.ndim
+        sl[axis] = slice(j, j + n)
+        out += w[j] * P[tuple(sl)]
+    return out
+
+
+def doh_response(I, s: float) -> np.ndarray:
+    """D per voxel ([z, y, x]; each z slice filtered on its own)."""
+    I = _vol(I)
+    _, g, g1, g2 = deriv_taps(s)
+    Ixx = _corr_axis(_corr_axis(I, g2, 2), g, 1)
+    Iyy = _corr_axis(_corr_axis(I, g, 2), g2, 1)
+    Ixy = _corr_axis(_corr_axis(I, g1, 2), g1, 1)
+    D = s ** 4 * (Ixx * Iyy - Ixy * Ixy)
+    return np.where(Ixx + Iyy < 0.0, D, -np.inf)
+
+
+def doh_seeds(I, s: float, rel_threshold: float) -> np.ndarray:
+    """Boolean seed mask."""
+    D = doh_response(I, s)
+    nz, ny, nx = D.shape
+    smax = D.reshape(nz, -1).max(axis=1)
+    seeds = (D > rel_threshold * smax[:, None, None]) & (smax[:, None, None] > 0.0)
+    P = np.pad(D, ((0, 0), (1, 1), (1, 1)), constant_values=-np.inf)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            if dy == 0 and dx == 0:
+                continue
+            seeds &= D > P[:, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+    return seeds
+
+
+def seed_phi0(shape, seeds_zyx: np.ndarray, r0: float) -> np.ndarray:
+    """phi0 = r0 - (Euclidean distance to the nearest seed), by brute force."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    best = np.full(shape, np.inf)
+    for sz, sy, sx in np.asarray(seeds_zyx, dtype=np.int64):
+        best = np.minimum(best, (z - sz) ** 2 + (y - sy) ** 2 + (x - sx) ** 2)
+    return r0 - np.sqrt(best)
