@@ -423,6 +423,37 @@ def run_serve(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_init(args, rank, world, local):
+    """The seed initialisation (Sec. 4.3) on the 512^3 light-sheet volume: blob seeds
+    per z slice and phi0 = r0 - distance to the nearest seed; metric GVoxel/s."""
+    from paper_2404_02813_gb300 import synth
+    vol = synth.lightsheet_volume_u16((args.size or 512,) * 3, brick=rank)
+    import torch
+    from paper_2404_02813_gb300 import rsf
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    ctx = rsf.Context(local)
+    v = torch.from_numpy(vol).cuda()
+    s, t, r0 = 1.5, 0.3, 2.0
+    for _ in range(max(args.warmup, 1)):
+        _, nseeds = ctx.init_phi0(v, s, t, r0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.init_phi0(v, s, t, r0)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    line = {"metric": "GVoxel/s (initialisation)", "value": vol.size / dt / 1e9, "unit": "GVoxel/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (light-sheet-like)",
+            "config": {"workload": f"init: {vol.shape[2]}x{vol.shape[1]}x{vol.shape[0]} uint16, determinant-of-"
+                                   f"Hessian seeds per z slice (s = {s}, t = {t}), phi0 = {r0} - exact distance",
+                       "seeds": nseeds, "timing": "host wall clock around the blocking call, inputs on the device"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def workload_desc(name, vol, params, iters):
     nz, ny, nx = vol.shape
     return {"workload": f"{name}: plain RSF, {nx}x{ny}x{nz} {vol.dtype.name} synthetic vessel volume, "
@@ -511,7 +542,7 @@ def main():
     ap.add_argument("--impl", default="rsf", choices=["rsf", "reference"])
     ap.add_argument("--workload", default="lightsheet512",
                     choices=["lightsheet512", "lightsheet512_s5", "tree64", "milling1024", "paper500", "bricks256",
-                             "serve"])
+                             "serve", "init512"])
     ap.add_argument("--curtain", type=int, default=None,
                     help="evolve through the curtain scheme with sub-volumes of this edge (Sec. 4.1)")
     ap.add_argument("--curtain-width", type=int, default=None, help="curtain width (default round(3 sigma))")
@@ -540,6 +571,8 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload == "serve":
         return run_serve(args, rank, world, local)
+    if args.workload == "init512":
+        return run_init(args, rank, world, local)
 
     import torch
     import torch.distributed as dist

@@ -156,6 +156,34 @@ rsf_status rsf_evolve_curtain(rsf_ctx *ctx, const void *volume, rsf_dtype vt, in
                               int32_t curtain);
 
 /*
+ * rsf_init_phi0 -- the seed initialisation of Sec. 4.3: blob seeds from the
+ * determinant of the Hessian in every z slice, then phi0 = r0 - the Euclidean
+ * distance to the nearest seed (the distance the paper's fast sweeping
+ * approximates, here exact).
+ *   Taps of the sampled Gaussian and its first and second derivatives,
+ *   k = -R..R, R = round(3 s): g_k = exp(-k^2/2s^2)/sum, g'_k = -(k/s^2) g_k,
+ *   g''_k = (k^2/s^4 - 1/s^2) g_k; in-slice correlation with zero padding:
+ *   I_xx = (g'' in x, g in y), I_yy = (g in x, g'' in y), I_xy = (g' in x,
+ *   g' in y); response D = s^4 (I_xx I_yy - I_xy^2) where I_xx + I_yy < 0,
+ *   else -inf.  A voxel is a seed when D > t * (maximum of D over its slice),
+ *   that maximum > 0, and D exceeds D at each existing in-slice neighbour.
+ *   blob_sigma     s > 0 with round(3 s) <= 16
+ *   rel_threshold  t in [0, 1)
+ *   r0             > 0, the radius of the initial regions around the seeds
+ *   phi0_out       nx*ny*nz floats, host or device
+ *   nseeds         receives the number of seeds
+ *   seeds_out      optional nx*ny*nz bytes, 1 at seeds (host or device, or NULL)
+ *   response_out   optional nx*ny*nz floats, D (host or device, or NULL)
+ * Dimensions: nx, ny in [4, 2^20], nz in [1, 2^20], with the largest squared
+ * distance below 2^24 (it is then exact in FP32).  Blocking.
+ * Errors: RSF_E_INVAL (arguments; no seed found: phi0_out is left untouched,
+ * seeds_out and response_out are written), RSF_E_NOMEM, RSF_E_CUDA.
+ */
+rsf_status rsf_init_phi0(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
+                         float blob_sigma, float rel_threshold, float r0, float *phi0_out, int64_t *nseeds,
+                         uint8_t *seeds_out, float *response_out);
+
+/*
  * rsf_step_stages -- one iteration from phi with the intermediate fields
  * written out, for checking each stage against a reference.
  *   stages   host or device buffer of RSF_NSTAGES * nx*ny*nz floats,

@@ -313,7 +313,11 @@ def doh_response(I, s: float) -> np.ndarray:
 
 def doh_seeds(I, s: float, rel_threshold: float) -> np.ndarray:
     """Boolean seed mask."""
-    D = doh_response(I, s)
+    return seeds_from_response(doh_response(I, s), rel_threshold)
+
+
+def seeds_from_response(D: np.ndarray, rel_threshold: float) -> np.ndarray:
+    """The seed rule applied to a response field D ([z, y, x])."""
     nz, ny, nx = D.shape
     smax = D.reshape(nz, -1).max(axis=1)
     seeds = (D > rel_threshold * smax[:, None, None]) & (smax[:, None, None] > 0.0)

@@ -27,7 +27,7 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
-            "rsf_serve_stats", "rsf_evolve_curtain")
+            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
@@ -103,6 +103,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_evolve_batch.restype = i32
     L.rsf_evolve_curtain.argtypes = [vp, vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, i32, i32]
     L.rsf_evolve_curtain.restype = i32
+    L.rsf_init_phi0.argtypes = [vp, vp, i32, i64, i64, i64, f32, f32, f32, vp, ctypes.POINTER(i64), vp, vp]
+    L.rsf_init_phi0.restype = i32
     L.rsf_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.rsf_submit.restype = i32
     L.rsf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
@@ -245,6 +247,22 @@ class Context:
         _check(load_library().rsf_evolve_curtain(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz, _ptr(phi0),
                                                  _ptr(out), *p.tuple(), int(iters), int(edge), int(curtain)))
         return out
+
+    def init_phi0(self, volume, blob_sigma: float, rel_threshold: float, r0: float, seeds=None, response=None):
+        """rsf_init_phi0: returns (phi0, number of seeds); `seeds` (uint8) and `response`
+        (float32), shaped like the volume, receive the seed mask and the blob response."""
+        nz, ny, nx = _shape(volume)
+        if hasattr(volume, "new_empty"):
+            phi0 = volume.new_empty((nz, ny, nx), dtype=__import__("torch").float32)
+        else:
+            phi0 = np.empty((nz, ny, nx), dtype=np.float32)
+        count = ctypes.c_int64(0)
+        _order_after_caller(volume, phi0)
+        _check(load_library().rsf_init_phi0(self._h, _ptr(volume), _vol_dtype(volume), nx, ny, nz,
+                                            float(blob_sigma), float(rel_threshold), float(r0), _ptr(phi0),
+                                            ctypes.byref(count), _ptr(seeds) if seeds is not None else None,
+                                            _ptr(response) if response is not None else None))
+        return phi0, int(count.value)
 
     def step_stages(self, volume, phi, params, phi_next=None, stages=None):
         """One iteration with the stage fields; returns (phi_next, stages[5, nz, ny, nx])."""
