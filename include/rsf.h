@@ -184,6 +184,16 @@ rsf_status rsf_init_phi0(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t
                          uint8_t *seeds_out, float *response_out);
 
 /*
+ * rsf_overlap -- segmentation scores (the paper's Dice coefficient and Jaccard
+ * index, Sec. 5.3): counts[0] = |phi > 0|, counts[1] = |truth != 0|,
+ * counts[2] = |phi > 0 and truth != 0| over n voxels.  Dice = 2 c2/(c0 + c1),
+ * Jaccard = c2/(c0 + c1 - c2).
+ *   phi, truth   n floats and n bytes, host or device.
+ * Blocking.  Errors: RSF_E_INVAL, RSF_E_NOMEM, RSF_E_CUDA.
+ */
+rsf_status rsf_overlap(rsf_ctx *ctx, const float *phi, const uint8_t *truth, int64_t n, int64_t counts[3]);
+
+/*
  * rsf_step_stages -- one iteration from phi with the intermediate fields
  * written out, for checking each stage against a reference.
  *   stages   host or device buffer of RSF_NSTAGES * nx*ny*nz floats,

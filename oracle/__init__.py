@@ -338,3 +338,19 @@ def seed_phi0(shape, seeds_zyx: np.ndarray, r0: float) -> np.ndarray:
     for sz, sy, sx in np.asarray(seeds_zyx, dtype=np.int64):
         best = np.minimum(best, (z - sz) ** 2 + (y - sy) ** 2 + (x - sx) ** 2)
     return r0 - np.sqrt(best)
+
+
+# ------------------------------------------------------- validation (Sec. 5.3)
+# The paper scores segmentations by the Dice coefficient and the Jaccard index
+# against annotations; here against the synthetic generators' ground truth.
+
+def overlap_counts(phi, truth) -> tuple:
+    """(|phi > 0|, |truth|, |phi > 0 and truth|)."""
+    seg = np.asarray(phi) > 0
+    t = np.asarray(truth).astype(bool)
+    return int(seg.sum()), int(t.sum()), int(np.logical_and(seg, t).sum())
+
+
+def dice_jaccard(counts) -> tuple:
+    a, b, c = counts
+    return (2.0 * c / (a + b) if a + b else 1.0), (c / (a + b - c) if a + b - c else 1.0)

@@ -237,3 +237,75 @@ extern "C" rsf_status rsf_init_phi0(rsf_ctx *c, const void *volume, rsf_dtype vt
     RSF_CUDA(cudaStreamSynchronize(s));
     return RSF_OK;
 }
+
+// ------------------------------------------------------------ validation
+
+namespace {
+
+// Counts |phi > 0|, |truth != 0| and their intersection (warp sums, one atomic
+// per warp per count).
+__global__ void k_overlap(const float *__restrict__ phi, const uint8_t *__restrict__ truth, long long n,
+                          unsigned long long *__restrict__ out) {
+    unsigned long long a = 0, b = 0, c = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const bool s = phi[i] > 0.f, t = truth[i] != 0;
+        a += s;
+        b += t;
+        c += s && t;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(out + 0, a);
+        atomicAdd(out + 1, b);
+        atomicAdd(out + 2, c);
+    }
+}
+
+}  // namespace
+
+extern "C" rsf_status rsf_overlap(rsf_ctx *c, const float *phi, const uint8_t *truth, int64_t n, int64_t counts[3]) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    if (!phi || !truth || !counts) return fail(RSF_E_INVAL, "null phi, truth or counts pointer");
+    if (n < 0 || n > (int64_t)1 << 34) return fail(RSF_E_INVAL, "n must lie in [0, 2^34]");
+    auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const bool host_phi = !on_device(phi), host_truth = !on_device(truth);
+    size_t bytes = 256 + (host_phi ? align(sizeof(float) * n) : 0) + (host_truth ? align(n) : 0);
+    void *mem = nullptr;
+    rsf_status st = dev_alloc(c, &mem, bytes);
+    if (st) return st;
+    struct Release {
+        rsf_ctx *c;
+        void *p;
+        size_t b;
+        ~Release() { dev_free(c, p, b); }
+    } release{c, mem, bytes};
+    char *p = static_cast<char *>(mem);
+    unsigned long long *out = reinterpret_cast<unsigned long long *>(p);
+    p += 256;
+    std::lock_guard<std::mutex> lk(c->mu);
+    RSF_CUDA(cudaSetDevice(c->device));
+    cudaStream_t s = c->stream;
+    if (host_phi) {
+        RSF_CUDA(cudaMemcpyAsync(p, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        phi = reinterpret_cast<const float *>(p);
+        p += align(sizeof(float) * n);
+    }
+    if (host_truth) {
+        RSF_CUDA(cudaMemcpyAsync(p, truth, n, cudaMemcpyHostToDevice, s));
+        truth = reinterpret_cast<const uint8_t *>(p);
+    }
+    RSF_CUDA(cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), s));
+    if (n > 0) {
+        k_overlap<<<(int)std::min<long long>(1216, (n + 255) / 256), 256, 0, s>>>(phi, truth, n, out);
+        RSF_CUDA(cudaGetLastError());
+    }
+    unsigned long long h[3];
+    RSF_CUDA(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s));
+    RSF_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < 3; ++k) counts[k] = (int64_t)h[k];
+    return RSF_OK;
+}

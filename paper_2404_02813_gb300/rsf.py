@@ -27,7 +27,7 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
-            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0")
+            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0", "rsf_overlap")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
@@ -105,6 +105,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_evolve_curtain.restype = i32
     L.rsf_init_phi0.argtypes = [vp, vp, i32, i64, i64, i64, f32, f32, f32, vp, ctypes.POINTER(i64), vp, vp]
     L.rsf_init_phi0.restype = i32
+    L.rsf_overlap.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
+    L.rsf_overlap.restype = i32
     L.rsf_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.rsf_submit.restype = i32
     L.rsf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
@@ -263,6 +265,21 @@ class Context:
                                             ctypes.byref(count), _ptr(seeds) if seeds is not None else None,
                                             _ptr(response) if response is not None else None))
         return phi0, int(count.value)
+
+    def overlap(self, phi, truth) -> dict:
+        """rsf_overlap: counts of phi > 0, truth and both, with Dice and Jaccard."""
+        n = 1
+        for d in _shape(phi):
+            n *= d
+        if _shape(truth) != _shape(phi):
+            raise ValueError("phi and truth shapes differ")
+        c = (ctypes.c_int64 * 3)()
+        _order_after_caller(phi, truth)
+        _check(load_library().rsf_overlap(self._h, _ptr(phi), _ptr(truth), n, c))
+        a, b, both = int(c[0]), int(c[1]), int(c[2])
+        return {"segmented": a, "truth": b, "both": both,
+                "dice": 2.0 * both / (a + b) if a + b else 1.0,
+                "jaccard": both / (a + b - both) if a + b - both else 1.0}
 
     def step_stages(self, volume, phi, params, phi_next=None, stages=None):
         """One iteration with the stage fields; returns (phi_next, stages[5, nz, ny, nx])."""

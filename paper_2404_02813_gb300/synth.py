@@ -188,20 +188,26 @@ def tree_volume_u8(shape_zyx=(64, 64, 64), workload: int = 1, brick: int = 0, n_
 
 def lightsheet_volume_u16(shape_zyx=(512, 512, 512), workload: int = 2, brick: int = 0,
                           n_segments: Optional[int] = None, r_range=(0.5, 3.0), peak: float = 4000.0,
-                          background: float = 300.0, psf_xy: float = 1.0, psf_z: float = 2.5) -> np.ndarray:
+                          background: float = 300.0, psf_xy: float = 1.0, psf_z: float = 2.5,
+                          truth: bool = False):
     """uint16 light-sheet-like volume: anisotropic PSF and Poisson shot noise.
 
     ~2000 segments per 512^3; smaller shapes scale the count with the volume.
+    With `truth`, also returns the ground-truth vessel mask: voxels whose
+    partial-volume occupancy (before the point-spread blur) is at least 1/2.
     """
     rng = rng_for(workload, brick)
     nz, ny, nx = shape_zyx
     if n_segments is None:
         n_segments = max(8, int(round(2000 * (nz * ny * nx) / 512 ** 3)))
     seg = vessel_segments(rng, (nx, ny, nz), n_segments, r_range)
-    occ = _blur(rasterize(seg, (0, 0, 0), shape_zyx), (psf_z, psf_xy, psf_xy))
+    occ0 = rasterize(seg, (0, 0, 0), shape_zyx)
+    mask = occ0 >= 0.5 if truth else None
+    occ = _blur(occ0, (psf_z, psf_xy, psf_xy))
+    del occ0
     lam = background + peak * occ
-    img = rng.poisson(lam)
-    return np.clip(img, 0, 65535).astype(np.uint16)
+    img = np.clip(rng.poisson(lam), 0, 65535).astype(np.uint16)
+    return (img, mask) if truth else img
 
 
 # ----------------------------------------------------- batched bricks
