@@ -185,7 +185,10 @@ template <int R, int NP>
 struct XYLayout {
     static constexpr int W = kXYT + 2 * R;              // loaded width
     static constexpr int H = kXYT + 2 * R;              // loaded rows
-    static constexpr int P = ((W + 15) / 16) * 16 + 1;  // row pitch = 1 (mod 16): conflict-free float2 reads
+    // row pitch = 2 (mod 16) float2: rows start 16-byte aligned, and the x pass's
+    // 16-byte window reads (lanes: 2 rows x 4 column groups per 8-lane phase) hit
+    // distinct banks
+    static constexpr int P = ((W + 15) / 16) * 16 + 2;
     static constexpr int IN = NP * H * P;               // input tile
     static constexpr int XC = NP * H * kXYT;            // x-convolved rows
     static constexpr size_t bytes = sizeof(float2) * (IN + XC);
@@ -207,7 +210,7 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
     constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
     constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
     constexpr int NE = (L::H * L::W + kXYThreads - 1) / kXYThreads;  // tile entries per thread
-    static_assert(NE <= 32, "tile entries per thread exceed the mask");
+    static_assert(NE <= 32, "too many tile entries per thread");
     float2 *in = sm;
     float2 *xc = sm + L::IN;
 
@@ -256,17 +259,26 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
                 const int row = (rem >> 1) * 8 + h * 4 + r;
                 const int xo = (rem & 1) * 16 + g * XT;
                 if (row < L::H) {
-                    const float2 *src = in + (p * L::H + row) * L::P + xo;
-                    float2 w[XT + 2 * R];
+                    const float4 *src = reinterpret_cast<const float4 *>(in + (p * L::H + row) * L::P + xo);
+                    // streamed: each loaded pair feeds the outputs it contributes to
+                    // (output o takes taps k = 0..T-1 in order, as a window would)
+                    float2 acc[XT];
 #pragma unroll
-                    for (int j = 0; j < XT + 2 * R; ++j) w[j] = src[j];
+                    for (int o = 0; o < XT; ++o) acc[o] = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int o = 0; o < XT; ++o) {
-                        float2 acc = make_float2(0.f, 0.f);
+                    for (int j2 = 0; j2 < (XT + 2 * R) / 2; ++j2) {
+                        const float4 q = src[j2];
 #pragma unroll
-                        for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
-                        xc[(p * L::H + row) * kXYT + xo + o] = acc;
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int j = 2 * j2 + h2;
+                            const float2 v = h2 ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+#pragma unroll
+                            for (int o = 0; o < XT; ++o)
+                                if (j - o >= 0 && j - o < T) acc[o] = f2fma(t.g[j - o], v, acc[o]);
+                        }
                     }
+#pragma unroll
+                    for (int o = 0; o < XT; ++o) xc[(p * L::H + row) * kXYT + xo + o] = acc[o];
                 }
             }
         }
@@ -276,15 +288,14 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
             float2 res[NP][YT];
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-                float2 w[YT + 2 * R];
 #pragma unroll
-                for (int j = 0; j < YT + 2 * R; ++j) w[j] = xc[(p * L::H + warp * YT + j) * kXYT + lane];
+                for (int o = 0; o < YT; ++o) res[p][o] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int o = 0; o < YT; ++o) {
-                    float2 acc = make_float2(0.f, 0.f);
+                for (int j = 0; j < YT + 2 * R; ++j) {
+                    const float2 v = xc[(p * L::H + warp * YT + j) * kXYT + lane];
 #pragma unroll
-                    for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
-                    res[p][o] = acc;
+                    for (int o = 0; o < YT; ++o)
+                        if (j - o >= 0 && j - o < T) res[p][o] = f2fma(t.g[j - o], v, res[p][o]);
                 }
             }
             if (gx < nx) {
