@@ -60,9 +60,9 @@ PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
 NCU_TRAFFIC = {
-    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "f908fef1f273ff37",
+    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "9c804633dcfcbf5c",
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
-    for k, v in {"rsf_ta_xy": 20.99, "rsf_ta_z": 23.42, "rsf_tb_xy": 15.19, "rsf_tb_z": 21.89}.items()
+    for k, v in {"rsf_ta_xy": 21.04, "rsf_ta_z": 23.42, "rsf_tb_xy": 15.22, "rsf_tb_z": 21.89}.items()
 }
 
 P_LIGHTSHEET = 4300.0
@@ -650,14 +650,25 @@ def main():
         step(vh, ph, oh)
         barrier()
         torch.cuda.synchronize()
+        eclocks = ClockSampler(local)
+        eclocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         t0 = time.perf_counter()
         for _ in range(args.steps):
             step(vh, ph, oh)
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, world)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eclk = eclocks.stop()
         e2e = {"value": whole_job_rate(rank_vox_it, world, te), "unit": "GVoxel-iterations/s",
                "h2d_bytes_per_step": int(vh.numel() * vh.element_size() + ph.numel() * 4),
-               "d2h_bytes_per_step": int(oh.numel() * 4)}
+               "d2h_bytes_per_step": int(oh.numel() * 4),
+               "ms_per_step": te * 1e3 / args.steps,
+               "stream_ms_per_step": e0.elapsed_time(e1) / args.steps,
+               "clocks": eclk}
 
     # the segmentation scored against the generator's ground truth (Dice, Jaccard; reported, not timed)
     seg = None
