@@ -92,3 +92,13 @@ def test_bad_arguments(ctx, s, t, r0):
     with pytest.raises(rsf.RSFError) as e:
         ctx.init_phi0(torch.from_numpy(vol).cuda(), s, t, r0)
     assert e.value.status == -1
+
+
+def test_host_arrays(ctx):
+    vol = synth.tree_volume_u8((10, 36, 40), n_segments=10)
+    phi_d, n_d, seeds_d, _ = _run(ctx, vol, 1.5, 0.2, 2.0)
+    seeds = np.zeros(vol.shape, dtype=np.uint8)
+    phi_h, n_h = ctx.init_phi0(vol, 1.5, 0.2, 2.0, seeds=seeds)
+    assert n_h == n_d
+    np.testing.assert_array_equal(seeds.astype(bool), seeds_d)
+    np.testing.assert_array_equal(phi_h, phi_d)
