@@ -354,3 +354,86 @@ def overlap_counts(phi, truth) -> tuple:
 def dice_jaccard(counts) -> tuple:
     a, b, c = counts
     return (2.0 * c / (a + b) if a + b else 1.0), (c / (a + b - c) if a + b - c else 1.0)
+
+
+# ------------------------------------------------- isosurface (Figs. 8-9)
+#
+# The zero level set as triangles, by marching tetrahedra: every voxel cube
+# (x..x+1, y..y+1, z..z+1) is split into six tetrahedra along its main
+# diagonal, one per order of the axes: corners 0, e_a, e_a + e_b, (1,1,1) for
+# the permutation (a, b, c).  In a tetrahedron with k corners where phi > iso:
+# k = 0 or 4, no triangle; k = 1 or 3, one triangle on the three edges that
+# join the odd corner to the others; k = 2, two triangles on the four crossed
+# edges (the quadrilateral p0 p1 q1 q0 split along p0-q1, in the order the
+# edges are listed below).  An edge (p, q), p the corner of smaller grid index,
+# is crossed at p + t (q - p), t = (iso - phi_p) / (phi_q - phi_p).  Each triangle is keyed by
+# (cube index) * 12 + (tetrahedron) * 2 + (triangle within it), the cube index
+# (z * (ny-1) + y) * (nx-1) + x, so that sets of triangles compare by key.
+# A grid value equal to iso counts as outside; the crossings of its edges then
+# meet at that corner and the triangles around it are degenerate.
+# Orientation: the normal (v1 - v0) x (v2 - v0) points from phi > iso towards
+# phi < iso (from the odd corner for k = 1, towards it for k = 3, from the
+# inside edge's midpoint to the outside edge's for k = 2); otherwise v1 and v2
+# are swapped.
+
+TETRA_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def _tetra_corners(perm):
+    c0 = (0, 0, 0)
+    c1 = [0, 0, 0]
+    c1[perm[0]] = 1
+    c2 = list(c1)
+    c2[perm[1]] = 1
+    return [c0, tuple(c1), tuple(c2), (1, 1, 1)]
+
+
+def isosurface(phi, iso: float = 0.0):
+    """(keys [T], triangles [T, 3, 3] as (x, y, z) points) of the phi = iso surface."""
+    phi = _vol(phi)
+    nz, ny, nx = phi.shape
+    keys, tris = [], []
+    for z in range(nz - 1):
+        for y in range(ny - 1):
+            for x in range(nx - 1):
+                base = ((z * (ny - 1) + y) * (nx - 1) + x) * 12
+                for t, perm in enumerate(TETRA_PERMS):
+                    cs = _tetra_corners(perm)
+                    pts = [np.array([x + c[0], y + c[1], z + c[2]], dtype=np.float64) for c in cs]
+                    val = [phi[z + c[2], y + c[1], x + c[0]] for c in cs]
+                    ins = [v > iso for v in val]
+                    k = sum(ins)
+                    if k in (0, 4):
+                        continue
+
+                    def cut(i, j):
+                        # from the corner with the smaller grid index, so that an edge
+                        # shared by several tetrahedra gives the same point in each
+                        if (cs[i][2], cs[i][1], cs[i][0]) > (cs[j][2], cs[j][1], cs[j][0]):
+                            i, j = j, i
+                        s = (iso - val[i]) / (val[j] - val[i])
+                        return pts[i] + s * (pts[j] - pts[i])
+
+                    def oriented(tri, out_dir):
+                        # normal (v1 - v0) x (v2 - v0) towards phi < iso
+                        nrm = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+                        return [tri[0], tri[2], tri[1]] if np.dot(nrm, out_dir) < 0 else tri
+
+                    if k in (1, 3):
+                        odd = ins.index(k == 1)
+                        others = [i for i in range(4) if i != odd]
+                        tri = [cut(odd, others[0]), cut(odd, others[1]), cut(odd, others[2])]
+                        out_dir = (tri[0] - pts[odd]) if k == 1 else (pts[odd] - tri[0])
+                        keys.append(base + 2 * t)
+                        tris.append(oriented(tri, out_dir))
+                    else:
+                        a = [i for i in range(4) if ins[i]]
+                        b = [i for i in range(4) if not ins[i]]
+                        p0, p1 = cut(a[0], b[0]), cut(a[0], b[1])
+                        q0, q1 = cut(a[1], b[0]), cut(a[1], b[1])
+                        out_dir = (pts[b[0]] + pts[b[1]] - pts[a[0]] - pts[a[1]]) / 2.0
+                        keys.append(base + 2 * t)
+                        tris.append(oriented([p0, p1, q1], out_dir))
+                        keys.append(base + 2 * t + 1)
+                        tris.append(oriented([p0, q1, q0], out_dir))
+    return np.array(keys, dtype=np.int64), np.array(tris, dtype=np.float64).reshape(-1, 3, 3)
