@@ -194,6 +194,27 @@ rsf_status rsf_init_phi0(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64_t
 rsf_status rsf_overlap(rsf_ctx *ctx, const float *phi, const uint8_t *truth, int64_t n, int64_t counts[3]);
 
 /*
+ * rsf_isosurface -- the phi = iso surface as triangles (the surfaces the paper
+ * renders, Figs. 8-9), by marching tetrahedra: every voxel cube is split into
+ * six tetrahedra along its main diagonal (corners 0, e_a, e_a + e_b, (1,1,1)
+ * for each order of the axes); a tetrahedron with 1 or 3 corners where
+ * phi > iso gives one triangle, with 2 such corners two; edges are cut by
+ * linear interpolation from their corner of smaller grid index; the normal
+ * (v1 - v0) x (v2 - v0) points from phi > iso towards phi < iso.
+ *   phi          nx*ny*nz floats, host or device; dimensions >= 2.
+ *   triangles    capacity * 9 floats (x, y, z of three vertices, voxel units),
+ *                host or device, or NULL with capacity 0 to count only.
+ *   keys         optional capacity int64: (cube index) * 12 + (tetrahedron) * 2
+ *                + (triangle), cube index (z*(ny-1) + y)*(nx-1) + x.
+ *   ntriangles   receives the number of triangles of the surface; when it
+ *                exceeds capacity only `capacity` of them are written.
+ * The set of triangles is deterministic; their order in the output is not.
+ * Blocking.  Errors: RSF_E_INVAL, RSF_E_NOMEM, RSF_E_CUDA.
+ */
+rsf_status rsf_isosurface(rsf_ctx *ctx, const float *phi, int64_t nx, int64_t ny, int64_t nz, float iso,
+                          float *triangles, int64_t *keys, int64_t capacity, int64_t *ntriangles);
+
+/*
  * rsf_step_stages -- one iteration from phi with the intermediate fields
  * written out, for checking each stage against a reference.
  *   stages   host or device buffer of RSF_NSTAGES * nx*ny*nz floats,

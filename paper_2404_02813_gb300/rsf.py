@@ -27,7 +27,7 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
-            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0", "rsf_overlap")
+            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0", "rsf_overlap", "rsf_isosurface")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_init_phi0.restype = i32
     L.rsf_overlap.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
     L.rsf_overlap.restype = i32
+    L.rsf_isosurface.argtypes = [vp, vp, i64, i64, i64, f32, vp, vp, i64, ctypes.POINTER(i64)]
+    L.rsf_isosurface.restype = i32
     L.rsf_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
     L.rsf_submit.restype = i32
     L.rsf_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]
@@ -280,6 +282,21 @@ class Context:
         return {"segmented": a, "truth": b, "both": both,
                 "dice": 2.0 * both / (a + b) if a + b else 1.0,
                 "jaccard": both / (a + b - both) if a + b - both else 1.0}
+
+    def isosurface(self, phi, iso: float = 0.0, with_keys: bool = True):
+        """rsf_isosurface: (triangles [T, 3, 3] as x, y, z, keys [T]) as numpy arrays."""
+        nz, ny, nx = _shape(phi)
+        count = ctypes.c_int64(0)
+        _order_after_caller(phi)
+        L = load_library()
+        _check(L.rsf_isosurface(self._h, _ptr(phi), nx, ny, nz, float(iso), None, None, 0, ctypes.byref(count)))
+        cap = int(count.value)
+        tri = np.empty((cap, 3, 3), dtype=np.float32)
+        keys = np.empty(cap, dtype=np.int64) if with_keys else None
+        if cap:
+            _check(L.rsf_isosurface(self._h, _ptr(phi), nx, ny, nz, float(iso), tri.ctypes.data,
+                                    keys.ctypes.data if with_keys else None, cap, ctypes.byref(count)))
+        return tri, keys
 
     def step_stages(self, volume, phi, params, phi_next=None, stages=None):
         """One iteration with the stage fields; returns (phi_next, stages[5, nz, ny, nx])."""
