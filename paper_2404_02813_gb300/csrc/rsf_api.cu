@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -256,6 +257,65 @@ bool on_device(const void *p) {
 
 size_t dtype_size(rsf_dtype vt) { return vt == RSF_U8 ? 1 : (vt == RSF_U16 ? 2 : 4); }
 
+namespace {
+__global__ void k_copy16(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void k_copy4(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void k_copy1(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+// 0 device or managed, 1 pinned host (allocated or registered with CUDA, with its
+// device address), 2 any other host memory (pageable, also where the device can
+// reach it through the address translation of the host)
+int mem_kind(const void *p, const void **dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 2;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+        *dev = p;
+        return 0;
+    }
+    unsigned flags = 0;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer && cudaHostGetFlags(&flags, const_cast<void *>(p)) == cudaSuccess) {
+        *dev = a.devicePointer;
+        return 1;
+    }
+    cudaGetLastError();
+    return 2;
+}
+}  // namespace
+
+cudaError_t xfer(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    const void *ds = nullptr, *dd = nullptr;
+    const int ks = mem_kind(src, &ds), kd = mem_kind(dst, &dd);
+    if (ks == 2 || kd == 2 || (ks == 0 && kd == 0)) return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+    // pinned host on at least one side: the SMs copy through the device mapping, which keeps its
+    // full rate after long device work (the copy engine's rate drops there)
+    const uintptr_t a = reinterpret_cast<uintptr_t>(ds) | reinterpret_cast<uintptr_t>(dd);
+    if ((a & 15) == 0 && bytes % 16 == 0) {
+        const size_t n = bytes / 16;
+        k_copy16<<<(unsigned)std::min<size_t>(1216, (n + 511) / 512), 512, 0, s>>>(static_cast<const uint4 *>(ds),
+                                                                                  static_cast<uint4 *>(const_cast<void *>(dd)), n);
+    } else if ((a & 3) == 0 && bytes % 4 == 0) {
+        const size_t n = bytes / 4;
+        k_copy4<<<(unsigned)std::min<size_t>(1216, (n + 511) / 512), 512, 0, s>>>(
+            static_cast<const uint32_t *>(ds), static_cast<uint32_t *>(const_cast<void *>(dd)), n);
+    } else {
+        k_copy1<<<(unsigned)std::min<size_t>(1216, (bytes + 511) / 512), 512, 0, s>>>(
+            static_cast<const uint8_t *>(ds), static_cast<uint8_t *>(const_cast<void *>(dd)), bytes);
+    }
+    return cudaGetLastError();
+}
+
 // Device-resident copy of the volume (the caller's own pointer when it already is one).
 static rsf_status device_volume(rsf_ctx *c, const void *volume, rsf_dtype vt, long long n, const void **out) {
     if (on_device(volume)) {
@@ -271,7 +331,7 @@ static rsf_status device_volume(rsf_ctx *c, const void *volume, rsf_dtype vt, lo
         if (st) return st;
         c->staging_cap = bytes;
     }
-    RSF_CUDA(cudaMemcpyAsync(c->staging, volume, bytes, cudaMemcpyDefault, c->stream));
+    RSF_CUDA(xfer(c->staging, volume, bytes, c->stream));
     *out = c->staging;
     return RSF_OK;
 }
@@ -401,7 +461,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
                     c->opt_path);
     // the tiled path reads the image in its own type and centres it on load
     RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream, !tiled));
-    RSF_CUDA(cudaMemcpyAsync(f.phi[0], phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    RSF_CUDA(xfer(f.phi[0], phi0, sizeof(float) * n, c->stream));
     RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
     int cur = 0;
     if (tiled) {
@@ -457,9 +517,9 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
             cur ^= 1;
         }
     }
-    RSF_CUDA(cudaMemcpyAsync(phi_out, f.phi[cur], sizeof(float) * n, cudaMemcpyDefault, c->stream));
+    RSF_CUDA(xfer(phi_out, f.phi[cur], sizeof(float) * n, c->stream));
     if (stages && dump != stages)
-        RSF_CUDA(cudaMemcpyAsync(stages, dump, sizeof(float) * n * RSF_NSTAGES, cudaMemcpyDefault, c->stream));
+        RSF_CUDA(xfer(stages, dump, sizeof(float) * n * RSF_NSTAGES, c->stream));
     int err_word = 0;
     RSF_CUDA(cudaMemcpyAsync(&err_word, f.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RSF_CUDA(cudaStreamSynchronize(c->stream));

@@ -203,7 +203,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         rsf::tiled_stage_views(storage, take(rsf::tiled_stage_bytes(storage, np)), np, &d.u4, &d.ab, &d.abxy);
         if (stage_img[i]) {
             void *img = take(dtype_size(b.vt) * n);
-            RSF_CUDA(cudaMemcpyAsync(img, b.volume, dtype_size(b.vt) * n, cudaMemcpyDefault, c->stream));
+            RSF_CUDA(xfer(img, b.volume, dtype_size(b.vt) * n, c->stream));
             d.img = img;
         } else {
             d.img = b.volume;
@@ -221,7 +221,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         f.cs = cs;
         f.prof = prof;
         RSF_CUDA(rsf::setup_image(d.img, (int)b.vt, make_taps(b.sigma), f, c->stream, false));
-        RSF_CUDA(cudaMemcpyAsync(d.phi[0], b.phi0, sizeof(float) * n, cudaMemcpyDefault, c->stream));
+        RSF_CUDA(xfer(d.phi[0], b.phi0, sizeof(float) * n, c->stream));
         if (b.iters > 0) RSF_CUDA(rsf::tiled_q_init(d.phi[0], d.q[0], n, b.eps, c->stream));
     }
 
@@ -232,8 +232,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
     auto retire = [&](int t) -> rsf_status {
         for (int i = 0; i < nb; ++i)
             if (bs[i].iters == t)
-                RSF_CUDA(cudaMemcpyAsync(bs[i].phi_out, bs[i].d.phi[t & 1], sizeof(float) * bs[i].n, cudaMemcpyDefault,
-                                         c->stream));
+                RSF_CUDA(xfer(bs[i].phi_out, bs[i].d.phi[t & 1], sizeof(float) * bs[i].n, c->stream));
         return RSF_OK;
     };
     rsf_status st = retire(0);

@@ -71,6 +71,9 @@ rsf_status cuda_fail(cudaError_t e, const char *what);
 rsf_status dev_alloc(rsf_ctx *c, void **p, size_t bytes);
 void dev_free(rsf_ctx *c, void *p, size_t bytes);
 bool on_device(const void *p);
+// Copy `bytes` on stream s between any two of device, pinned host and pageable
+// host memory; pinned host memory is read or written by a copy kernel.
+cudaError_t xfer(void *dst, const void *src, size_t bytes, cudaStream_t s);
 size_t dtype_size(rsf_dtype vt);
 rsf_status check_args(const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz, const void *phi0,
                       const void *phi_out, float sigma, float eps, float dt, int32_t iters);

@@ -181,12 +181,12 @@ extern "C" rsf_status rsf_evolve_curtain(rsf_ctx *c, const void *volume, rsf_dty
         const float *ph0 = phi0;
         if (host_vol) {
             void *d = take(es * nvox);
-            RSF_CUDA(cudaMemcpyAsync(d, volume, es * nvox, cudaMemcpyHostToDevice, c->stream));
+            RSF_CUDA(xfer(d, volume, es * nvox, c->stream));
             vol = d;
         }
         if (host_phi) {
             float *d = reinterpret_cast<float *>(take(sizeof(float) * nvox));
-            RSF_CUDA(cudaMemcpyAsync(d, phi0, sizeof(float) * nvox, cudaMemcpyHostToDevice, c->stream));
+            RSF_CUDA(xfer(d, phi0, sizeof(float) * nvox, c->stream));
             ph0 = d;
         }
         for (int kz = 0; kz < nb[2]; ++kz)
@@ -251,7 +251,7 @@ extern "C" rsf_status rsf_evolve_curtain(rsf_ctx *c, const void *volume, rsf_dty
     RSF_CUDA(cudaMemcpyAsync(tb, host_tab.data(), off, cudaMemcpyHostToDevice, c->stream));
     k_merge<<<(int)std::min<long long>(4864, (nvox + 255) / 256), 256, 0, c->stream>>>(m, out);
     RSF_CUDA(cudaGetLastError());
-    if (host_out) RSF_CUDA(cudaMemcpyAsync(phi_out, out, sizeof(float) * nvox, cudaMemcpyDeviceToHost, c->stream));
+    if (host_out) RSF_CUDA(xfer(phi_out, out, sizeof(float) * nvox, c->stream));
     RSF_CUDA(cudaStreamSynchronize(c->stream));
     return RSF_OK;
 }

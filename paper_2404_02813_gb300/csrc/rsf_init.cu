@@ -201,7 +201,7 @@ extern "C" rsf_status rsf_init_phi0(rsf_ctx *c, const void *volume, rsf_dtype vt
     const void *img = volume;
     if (host_vol) {
         void *d = take(es * n);
-        RSF_CUDA(cudaMemcpyAsync(d, volume, es * n, cudaMemcpyHostToDevice, s));
+        RSF_CUDA(xfer(d, volume, es * n, s));
         img = d;
     }
     const DerivTaps tp = make_deriv_taps(blob_sigma);
@@ -224,8 +224,8 @@ extern "C" rsf_status rsf_init_phi0(rsf_ctx *c, const void *volume, rsf_dtype vt
     RSF_CUDA(cudaMemcpyAsync(&found, count, sizeof(found), cudaMemcpyDeviceToHost, s));
     RSF_CUDA(cudaStreamSynchronize(s));
     *nseeds = (int64_t)found;
-    if (response_out) RSF_CUDA(cudaMemcpyAsync(response_out, D, sizeof(float) * n, cudaMemcpyDefault, s));
-    if (seeds_out) RSF_CUDA(cudaMemcpyAsync(seeds_out, mask, n, cudaMemcpyDefault, s));
+    if (response_out) RSF_CUDA(xfer(response_out, D, sizeof(float) * n, s));
+    if (seeds_out) RSF_CUDA(xfer(seeds_out, mask, n, s));
     if (found == 0) {
         RSF_CUDA(cudaStreamSynchronize(s));
         return fail(RSF_E_INVAL, "no seed found (relative threshold %g)", (double)rel_threshold);
@@ -233,7 +233,7 @@ extern "C" rsf_status rsf_init_phi0(rsf_ctx *c, const void *volume, rsf_dtype vt
     float *phi = host_phi ? t1 : phi0_out;
     k_phi0<<<grid, 256, 0, s>>>(t0, phi, n, r0);
     RSF_CUDA(cudaGetLastError());
-    if (host_phi) RSF_CUDA(cudaMemcpyAsync(phi0_out, phi, sizeof(float) * n, cudaMemcpyDeviceToHost, s));
+    if (host_phi) RSF_CUDA(xfer(phi0_out, phi, sizeof(float) * n, s));
     RSF_CUDA(cudaStreamSynchronize(s));
     return RSF_OK;
 }
@@ -290,12 +290,12 @@ extern "C" rsf_status rsf_overlap(rsf_ctx *c, const float *phi, const uint8_t *t
     RSF_CUDA(cudaSetDevice(c->device));
     cudaStream_t s = c->stream;
     if (host_phi) {
-        RSF_CUDA(cudaMemcpyAsync(p, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        RSF_CUDA(xfer(p, phi, sizeof(float) * n, s));
         phi = reinterpret_cast<const float *>(p);
         p += align(sizeof(float) * n);
     }
     if (host_truth) {
-        RSF_CUDA(cudaMemcpyAsync(p, truth, n, cudaMemcpyHostToDevice, s));
+        RSF_CUDA(xfer(p, truth, n, s));
         truth = reinterpret_cast<const uint8_t *>(p);
     }
     RSF_CUDA(cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), s));

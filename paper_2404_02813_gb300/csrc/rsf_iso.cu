@@ -182,7 +182,7 @@ extern "C" rsf_status rsf_isosurface(rsf_ctx *c, const float *phi, int64_t nx, i
     cudaStream_t s = c->stream;
     const float *ph = phi;
     if (host_phi) {
-        RSF_CUDA(cudaMemcpyAsync(p, phi, sizeof(float) * n, cudaMemcpyHostToDevice, s));
+        RSF_CUDA(xfer(p, phi, sizeof(float) * n, s));
         ph = reinterpret_cast<const float *>(p);
         p += align(sizeof(float) * n);
     }
@@ -203,9 +203,9 @@ extern "C" rsf_status rsf_isosurface(rsf_ctx *c, const float *phi, int64_t nx, i
     *ntriangles = (int64_t)count;
     const long long written = std::min<long long>((long long)count, capacity);
     if (host_tri && written > 0)
-        RSF_CUDA(cudaMemcpyAsync(triangles, e.tri, sizeof(float) * 9 * written, cudaMemcpyDeviceToHost, s));
+        RSF_CUDA(xfer(triangles, e.tri, sizeof(float) * 9 * written, s));
     if (host_keys && written > 0)
-        RSF_CUDA(cudaMemcpyAsync(keys, e.keys, sizeof(long long) * written, cudaMemcpyDeviceToHost, s));
+        RSF_CUDA(xfer(keys, e.keys, sizeof(long long) * written, s));
     RSF_CUDA(cudaStreamSynchronize(s));
     return RSF_OK;
 }

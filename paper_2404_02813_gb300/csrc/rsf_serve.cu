@@ -213,7 +213,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     rsf::tiled_stage_views(r->storage, take(rsf::tiled_stage_bytes(r->storage, np)), np, &d.u4, &d.ab, &d.abxy);
     if (stage_img) {
         void *img = take(dtype_size(q.vt) * n);
-        if (cudaMemcpyAsync(img, q.volume, dtype_size(q.vt) * n, cudaMemcpyDefault, s->s_setup) != cudaSuccess)
+        if (xfer(img, q.volume, dtype_size(q.vt) * n, s->s_setup) != cudaSuccess)
             return fail_admit(RSF_E_CUDA);
         d.img = img;
     } else {
@@ -242,7 +242,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
         memcpy(ch.v, pr.data() + o, sizeof(float) * ch.count);
         k_put<<<(ch.count + 255) / 256, 256, 0, s->s_setup>>>(ch, prof);
     }
-    if (cudaMemcpyAsync(d.phi[0], q.phi0, sizeof(float) * n, cudaMemcpyDefault, s->s_setup) != cudaSuccess)
+    if (xfer(d.phi[0], q.phi0, sizeof(float) * n, s->s_setup) != cudaSuccess)
         return fail_admit(RSF_E_CUDA);
     if (q.iters > 0 && rsf::tiled_q_init(d.phi[0], d.q[0], n, q.eps, s->s_setup) != cudaSuccess)
         return fail_admit(RSF_E_CUDA);
@@ -260,8 +260,7 @@ void retire(Server *s, const std::shared_ptr<Request> &r, bool cancelled) {
     int st = RSF_OK;
     if (cancelled) {
         st = RSF_E_CANCELLED;
-    } else if (cudaMemcpyAsync(r->req.phi_out, r->d.phi[r->req.iters & 1], sizeof(float) * r->n, cudaMemcpyDefault,
-                               s->s_comp) != cudaSuccess) {
+    } else if (xfer(r->req.phi_out, r->d.phi[r->req.iters & 1], sizeof(float) * r->n, s->s_comp) != cudaSuccess) {
         st = RSF_E_CUDA;
     }
     cudaLaunchHostFunc(s->s_comp, done_cb, new DoneArg{s, r, st});

@@ -203,6 +203,7 @@ class Context:
         _check(L.rsf_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), 0))
         self._h = h
         self.device = int(device)
+        self._live = {}  # ticket -> the submitted buffers, kept alive while the library uses them
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -352,16 +353,31 @@ class Context:
                     STORAGE[storage], int(halo), int(stream.cuda_stream) if stream is not None else 0)
         t = ctypes.c_uint64()
         _check(load_library().rsf_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._live[int(t.value)] = (volume, phi0, out)  # the library reads and writes them until the ticket resolves
         return int(t.value)
 
     def poll(self, ticket: int):
         """(status, latency_s): status RSF_PENDING (1) or RSF_OK (0); errors raise."""
         lat = ctypes.c_double(-1.0)
-        st = _check(load_library().rsf_poll(self._h, int(ticket), ctypes.byref(lat)))
+        try:
+            st = _check(load_library().rsf_poll(self._h, int(ticket), ctypes.byref(lat)))
+        except RSFError:
+            self._live.pop(int(ticket), None)
+            raise
+        if st != 1:
+            self._live.pop(int(ticket), None)
         return st, lat.value
 
     def wait(self, ticket: int, timeout_ms: int = -1):
-        return _check(load_library().rsf_wait(self._h, int(ticket), int(timeout_ms)))
+        try:
+            st = _check(load_library().rsf_wait(self._h, int(ticket), int(timeout_ms)))
+        except RSFError as e:
+            if e.status != -4:  # not a timeout: the ticket is resolved
+                self._live.pop(int(ticket), None)
+            raise
+        if st != 1:
+            self._live.pop(int(ticket), None)
+        return st
 
     def cancel(self, ticket: int):
         _check(load_library().rsf_cancel(self._h, int(ticket)))

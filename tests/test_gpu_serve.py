@@ -93,7 +93,8 @@ def test_cancel_and_host_buffers(cases):
     ctx = rsf.Context(0)
     vol, phi0, p, _, _ = cases[0]
     long_out = np.zeros_like(phi0)
-    t_long = ctx.submit(vol, phi0.copy(), p, 100000, long_out)  # host buffers
+    long_start = phi0.copy()
+    t_long = ctx.submit(vol, long_start, p, 100000, long_out)  # host buffers
     time.sleep(0.05)
     ctx.cancel(t_long)
     with pytest.raises(rsf.RSFError) as e:
@@ -102,7 +103,8 @@ def test_cancel_and_host_buffers(cases):
     assert not long_out.any()  # a cancelled request does not write phi_out
     # the loop keeps serving after a cancellation
     out = np.zeros_like(phi0)
-    t = ctx.submit(vol, phi0.copy(), p, 4, out)
+    start = phi0.copy()  # the caller keeps its buffers until the ticket resolves
+    t = ctx.submit(vol, start, p, 4, out)
     assert ctx.wait(t, 60000) == 0
     ref = rsf.Context(0).evolve(vol, phi0.copy(), p, 4)
     np.testing.assert_array_equal(out, ref)
