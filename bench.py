@@ -43,14 +43,14 @@ def algo_bytes_per_voxel(img: int, st: int, force: str = "li") -> dict:
         "rsf_a_x": 4 + 4 + 16, "rsf_a_y": 16 + 16, "rsf_a_z": 16 + 8,
         "rsf_b_x": 8 + 8, "rsf_b_y": 8 + 8, "rsf_b_z": 8 + 4 + 4 + 4,
         # tiled schedule
-        "rsf_ta_xy": 4 + img + 4 * st,          # q, I -> four group-A fields
-        "rsf_ta_z": 4 * st + ab_out,            # four fields -> (a, b)
+        "rsf_ta_xy": 4 + img + 8,               # q, I -> x/y-convolved (H I~, H), FP32
+        "rsf_ta_z": 8 + 4 + ab_out,             # (H I~, H), K*I~ -> (a, b)
         "rsf_tb_xy": 2 * st + 8,                # (a, b) -> x/y-convolved (a, b), FP32
         "rsf_tb_z": 8 + img + 4 + 4 + 4,        # (a, b)_xy, I, phi -> phi', q(phi')
     }
 
 
-SETUP_LAUNCHES = 3  # statistics, their reduction, q of phi0
+SETUP_LAUNCHES = 5  # statistics, their reduction, q of phi0, K*I~ (x/y pass, z pass)
 NOMINAL_HBM_GBS = 7900.0
 # The paper's Table 1: one time step on a 500^3 volume takes 585 ms summed over
 # its kernels (Eq. (15) form, sigma_2 = 0), i.e. 1.25e8 / 0.585 s voxel-iterations/s.
@@ -728,7 +728,7 @@ def main():
         traffic = (tr["bytes_per_voxel"] * n_vox
                    if tr and same_case and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
         launches = sum(n for n, _ in prof.values()) + (SETUP_LAUNCHES * args.steps if not args.curtain
-                                                       else (5 * nbox + 1) * args.steps)
+                                                       else (7 * nbox + 1) * args.steps)
         line = {
             "metric": "GVoxel-iterations/s", "value": value, "unit": "GVoxel-iterations/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,

@@ -478,7 +478,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         b.phi[1] = f.phi[1];
         b.q[0] = f.q[0];
         b.q[1] = f.q[1];
-        rsf::tiled_stage_views(storage, f.t[0], (long long)f.px * ny * nz, &b.u4, &b.ab, &b.abxy);
+        rsf::tiled_stage_views(storage, f.t[0], (long long)f.px * ny * nz, &b.u2, &b.ab, &b.abxy, &b.ki);
         b.eps = eps;
         b.lambda1 = lambda1;
         b.lambda2 = lambda2;
@@ -503,7 +503,10 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         std::vector<rsf::TiledGroup> groups;
         if ((st = upload_groups(c, c->desc, c->stream, specs, &groups))) return st;
         const rsf::TiledGroup &g = groups[0];
-        if (iters > 0) RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
+        if (iters > 0) {
+            RSF_CUDA(rsf::tiled_q_init(f.phi[0], f.q[0], n, eps, c->stream));
+            RSF_CUDA(rsf::tiled_ki_init(b, (int)vt, taps, c->stream));
+        }
         for (int it = 0; it < iters; ++it) {
             cudaError_t e = rsf::tiled_iterate(g, it & 1, &c->prof, c->stream);
             if (e != cudaSuccess) return cuda_fail(e, "iteration launch");

@@ -200,7 +200,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         d.prof = prof;
         d.cs = cs;
         const long long np = (long long)px * b.ny * b.nz;
-        rsf::tiled_stage_views(storage, take(rsf::tiled_stage_bytes(storage, np)), np, &d.u4, &d.ab, &d.abxy);
+        rsf::tiled_stage_views(storage, take(rsf::tiled_stage_bytes(storage, np)), np, &d.u2, &d.ab, &d.abxy, &d.ki);
         if (stage_img[i]) {
             void *img = take(dtype_size(b.vt) * n);
             RSF_CUDA(xfer(img, b.volume, dtype_size(b.vt) * n, c->stream));
@@ -222,7 +222,10 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         f.prof = prof;
         RSF_CUDA(rsf::setup_image(d.img, (int)b.vt, make_taps(b.sigma), f, c->stream, false));
         RSF_CUDA(xfer(d.phi[0], b.phi0, sizeof(float) * n, c->stream));
-        if (b.iters > 0) RSF_CUDA(rsf::tiled_q_init(d.phi[0], d.q[0], n, b.eps, c->stream));
+        if (b.iters > 0) {
+            RSF_CUDA(rsf::tiled_q_init(d.phi[0], d.q[0], n, b.eps, c->stream));
+            RSF_CUDA(rsf::tiled_ki_init(d, (int)b.vt, make_taps(b.sigma), c->stream));
+        }
     }
 
     // ---- iterate: fixed active sets between retirements

@@ -97,8 +97,10 @@ struct BrickDev {
     const float *cs;        // centring constants [m, 1/s, s^2, s]
     const float *prof;      // K*1 profiles p_x[nx], p_y[ny], p_z[nz]
     float *phi[2], *q[2];   // ping-pong level set and its q = +-atan(eps/|phi|)/pi
-    void *u4, *ab;          // pitched group-A fields (4 per voxel) and (a, b), storage type
-    float2 *abxy;           // pitched x/y-convolved (a, b), FP32
+    float2 *u2;             // pitched x/y-convolved (H I~, H), FP32
+    void *ab;               // pitched (a, b), storage type
+    float2 *abxy;           // pitched x/y-convolved (a, b), FP32 (also the set-up's scratch for ki)
+    float *ki;              // pitched K*I~ (the centred image convolved), FP32, set once per solve
     float eps, lambda1, lambda2, nu, mu, dt;
     int zc;                 // z chunk of the update kernel
     int flip;               // this brick's buffer parity is the launch parity xor flip
@@ -124,9 +126,11 @@ cudaError_t tiled_prepare(int storage, int R, int force);
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
 void tiled_cta_counts(const BrickDev &b, unsigned counts[4]);
 size_t tiled_stage_bytes(int storage, long long np);
-void tiled_stage_views(int storage, void *base, long long np, void **u4, void **ab, float2 **abxy);
+void tiled_stage_views(int storage, void *base, long long np, float2 **u2, void **ab, float2 **abxy, float **ki);
 // q = +-atan(eps/|phi|)/pi (sign of phi) before the first tiled iteration.
 cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s);
+// b.ki = K*I~ before the first tiled iteration (b.img, b.cs set; uses b.abxy as scratch).
+cudaError_t tiled_ki_init(const BrickDev &b, int imgtype, const Taps &taps, cudaStream_t s);
 
 // One iteration of the separable pass path: phi_in -> phi_out.
 // `stages`, when not null, receives RSF_NSTAGES fields (f1, f2, g, kappa, L).

@@ -210,7 +210,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     d.prof = prof;
     d.cs = cs;
     const long long np = (long long)px * q.ny * q.nz;
-    rsf::tiled_stage_views(r->storage, take(rsf::tiled_stage_bytes(r->storage, np)), np, &d.u4, &d.ab, &d.abxy);
+    rsf::tiled_stage_views(r->storage, take(rsf::tiled_stage_bytes(r->storage, np)), np, &d.u2, &d.ab, &d.abxy, &d.ki);
     if (stage_img) {
         void *img = take(dtype_size(q.vt) * n);
         if (xfer(img, q.volume, dtype_size(q.vt) * n, s->s_setup) != cudaSuccess)
@@ -245,6 +245,8 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     if (xfer(d.phi[0], q.phi0, sizeof(float) * n, s->s_setup) != cudaSuccess)
         return fail_admit(RSF_E_CUDA);
     if (q.iters > 0 && rsf::tiled_q_init(d.phi[0], d.q[0], n, q.eps, s->s_setup) != cudaSuccess)
+        return fail_admit(RSF_E_CUDA);
+    if (q.iters > 0 && rsf::tiled_ki_init(d, (int)q.vt, r->taps, s->s_setup) != cudaSuccess)
         return fail_admit(RSF_E_CUDA);
     if (rsf::tiled_prepare(r->storage, r->taps.R, r->force) != cudaSuccess) return fail_admit(RSF_E_CUDA);
     if (cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming) != cudaSuccess) return fail_admit(RSF_E_CUDA);

@@ -8,14 +8,17 @@
 // binary search over the per-kernel CTA offsets of the group.
 //
 //   rsf_ta_xy  per z-plane, a 32x32 output tile plus an R halo in shared
-//              memory: forms H I~, H, (1-H) I~, 1-H (Eqs. 6, 8-10) from the
-//              image (centred on load) and q = +-atan(eps/|phi|)/pi, convolves
-//              them along x then y (field pairs share packed f32x2 FMAs) and
-//              stores them (FP32, FP16 or BF16 storage).
-//   rsf_ta_z   x-z slabs (32 columns x 64 output planes) loaded into shared
-//              memory all at once; z convolution over a register window; the
-//              local fits f1 = K*(H I)/K*H, f2 = K*((1-H) I)/K*(1-H), and
-//              a = l1 f1 - l2 f2, b = l1 f1^2 - l2 f2^2.
+//              memory: forms H I~ and H (Eqs. 6, 8-10) from the image
+//              (centred on load) and q = +-atan(eps/|phi|)/pi, convolves the
+//              pair along x then y (packed f32x2 FMAs) and stores it (FP32).
+//   rsf_ta_z   x-z slabs (32 columns x 64 output planes) staged in shared
+//              memory by cp.async, two slabs in flight; z convolution over a
+//              register window; the local fits f1 = K*(H I~)/K*H and
+//              f2 = K*((1-H) I~)/K*(1-H), the latter from the linearity of the
+//              convolution as (K*I~ - K*(H I~)) / (K*1 - K*H) with K*I~ fixed
+//              for the solve (rsf_ki_xy / rsf_ki_z, once) and K*1 the product of
+//              the three 1-D zero-padding profiles; a = l1 f1 - l2 f2,
+//              b = l1 f1^2 - l2 f2^2 (stored FP32, FP16 or BF16).
 //   rsf_tb_xy  the x/y kernel on (a, b); its output stays FP32 (the data term
 //              below is a difference of terms much larger than itself).
 //   rsf_tb_z   a z march over a 32x8 column tile: a register ring of (a, b)
@@ -145,7 +148,7 @@ struct GroupArgs {
 // element offset `off`, fetch(plane, o) the raw values at offset o within it,
 // apply() the NP float2 pairs (zero outside the brick).
 template <class ImgT>
-struct ProHP {  // (H I~, H), ((1-H) I~, 1-H) from q and the centred image
+struct ProH {  // (H I~, H) from q and the centred image
     const float *q;
     const ImgT *img;
     float inv_s, nms;
@@ -157,13 +160,24 @@ struct ProHP {  // (H I~, H), ((1-H) I~, 1-H) from q and the centred image
     }
     __device__ __forceinline__ Raw zero() const { return Raw{0.f, 0.f}; }
     __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
-        if (inside) {
-            const float h = h_of_q(r.q), hc = hc_of_q(r.q);
-            v[0] = make_float2(h * r.im, h);
-            v[1] = make_float2(hc * r.im, hc);
-        } else {
-            v[0] = v[1] = make_float2(0.f, 0.f);
-        }
+        const float h = h_of_q(r.q);
+        v[0] = inside ? make_float2(h * r.im, h) : make_float2(0.f, 0.f);
+    }
+};
+
+template <class ImgT>
+struct ProI {  // (I~, 0): the centred image alone, for K*I~
+    const ImgT *img;
+    float inv_s, nms;
+    using Raw = float;
+    struct Plane { const ImgT *img; };
+    __device__ __forceinline__ Plane plane(long long off) const { return Plane{img + off}; }
+    __device__ __forceinline__ Raw fetch(const Plane &pl, int o) const {
+        return fmaf((float)__ldg(pl.img + o), inv_s, nms);
+    }
+    __device__ __forceinline__ Raw zero() const { return 0.f; }
+    __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
+        v[0] = make_float2(inside ? r : 0.f, 0.f);
     }
 };
 
@@ -312,21 +326,11 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
 
 // Writers of the x/y kernel's outputs: plane(z) gives plane z, operator()
 // stores at offset y * px + x within it.
-template <class S>
-struct OutU4 {  // four H-product fields -> pitched storage
-    typename Store<S>::V4 *u;
+struct OutF2 {  // one x/y-convolved pair, FP32, pitched
+    float2 *u;
     int px;
     long long pplane;
-    __device__ __forceinline__ typename Store<S>::V4 *plane(int z) const { return u + (long long)z * pplane; }
-    __device__ __forceinline__ void operator()(typename Store<S>::V4 *pl, int o, float2 a, float2 b) const {
-        pl[o] = Store<S>::pack4(make_float4(a.x, a.y, b.x, b.y));
-    }
-};
-struct OutAB {  // x/y-convolved (a, b), FP32, pitched
-    float2 *ab;
-    int px;
-    long long pplane;
-    __device__ __forceinline__ float2 *plane(int z) const { return ab + (long long)z * pplane; }
+    __device__ __forceinline__ float2 *plane(int z) const { return u + (long long)z * pplane; }
     __device__ __forceinline__ void operator()(float2 *pl, int o, float2 a, float2) const { pl[o] = a; }
 };
 
@@ -341,16 +345,16 @@ __device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev 
     return XYTile{b, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes};
 }
 
-template <int R, class ImgT, class S>
-__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 2>()) k_ta_xy(GroupArgs G, TapPairs t) {
+template <int R, class ImgT>
+__global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 2) k_ta_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
     const BrickDev B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
-    ProHP<ImgT> pro{(G.parity ^ B.flip) ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
-    OutU4<S> out{reinterpret_cast<typename Store<S>::V4 *>(B.u4), B.px, (long long)B.px * B.ny};
-    xy_tile<R, 2>(pro, out, B.nx, B.ny, B.nz, B.nx, tl.x0, tl.y0, tl.za, t, sm);
+    ProH<ImgT> pro{(G.parity ^ B.flip) ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
+    OutF2 out{B.u2, B.px, (long long)B.px * B.ny};
+    xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.nx, tl.x0, tl.y0, tl.za, t, sm);
 }
 
 template <int R, class S>
@@ -360,37 +364,31 @@ __global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 1>()) k_tb_xy(Gro
     const BrickDev B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
     ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
-    OutAB out{B.abxy, B.px, (long long)B.px * B.ny};
+    OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
     xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.px, tl.x0, tl.y0, tl.za, t, sm);
 }
 
 // ------------------------------------------------------------------ A: z
 
 // x-z slabs: 32 columns of one y row and kAZT output planes (plus the R-plane
-// halos).  A persistent CTA walks the slabs of the launch (consecutive slabs
-// are consecutive z ranges of one row, so shared halos hit L2) with a
-// two-stage shared-memory buffer: the cp.async copies of the next slab are in
-// flight while the current one is convolved.  Rows outside the brick are
-// zero-filled by the copy (source size 0).  FP32 storage splits each element's
-// two field pairs into two arrays (conflict-free 8-byte window reads); 16-bit
-// storage keeps the packed element and unpacks the pair it reads.
-template <class S> struct AZSlab;
-template <> struct AZSlab<float> {
-    static constexpr int kArrays = 2;
-};
-template <> struct AZSlab<__half> {
-    static constexpr int kArrays = 1;
-};
-template <> struct AZSlab<__nv_bfloat16> {
-    static constexpr int kArrays = 1;
-};
-
-template <int R, class S>
-constexpr size_t az_smem() { return 2 * sizeof(float2) * AZSlab<S>::kArrays * (kAZT + 2 * R) * 32; }
+// halos) of the x/y-convolved pair (H I~, H), and the kAZT planes of K*I~ the
+// slab's outputs use.  A persistent CTA walks the slabs of the launch
+// (consecutive slabs are consecutive z ranges of one row, so shared halos hit
+// L2) with a two-stage shared-memory buffer: the cp.async copies of the next
+// slab are in flight while the current one is convolved.  Rows outside the
+// brick are zero-filled by the copy (source size 0).
+template <int R>
+constexpr int az_stage() { return (kAZT + 2 * R) * 32 + kAZT * 16; }  // float2 units per stage
+template <int R>
+constexpr size_t az_smem() { return 2 * sizeof(float2) * az_stage<R>(); }
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -423,61 +421,50 @@ __device__ __forceinline__ AZSlabId az_slab_of(const GroupArgs &G, int slab) {
     return AZSlabId{b, xt * 32, y, zt * kAZT};
 }
 
-// Issues the copies of one slab into `buf` (ROWS x 32 elements per array).
-template <int R, class S>
+// Issues the copies of one slab into `buf`: ROWS x 32 pairs, then kAZT x 32
+// values of K*I~.  Columns past nx lie in the pitch padding (allocated).
+template <int R>
 __device__ __forceinline__ void az_issue(const GroupArgs &G, const AZSlabId &id, float2 *buf) {
     constexpr int ROWS = kAZT + 2 * R;
-    using V4 = typename Store<S>::V4;
     const BrickDev &B = G.bricks[id.b];
     const int col = threadIdx.x & 31;
     const long long pplane = (long long)B.px * B.ny;
-    const V4 *src = reinterpret_cast<const V4 *>(B.u4) + (long long)id.y * B.px + id.x0 + col;
+    const long long c0 = (long long)id.y * B.px + id.x0 + col;
     for (int row = threadIdx.x >> 5; row < ROWS; row += kAZThreads / 32) {
         const int zi = id.z0 - R + row;
         const bool ok = (unsigned)zi < (unsigned)B.nz;
-        const V4 *g = src + (long long)(ok ? zi : 0) * pplane;
-        if constexpr (AZSlab<S>::kArrays == 2) {
-            cp_async8(buf + row * 32 + col, g, ok);
-            cp_async8(buf + (ROWS + row) * 32 + col, reinterpret_cast<const char *>(g) + 8, ok);
-        } else {
-            cp_async8(buf + row * 32 + col, g, ok);
-        }
+        cp_async8(buf + row * 32 + col, B.u2 + c0 + (long long)(ok ? zi : 0) * pplane, ok);
+    }
+    float *kb = reinterpret_cast<float *>(buf + ROWS * 32);
+    for (int row = threadIdx.x >> 5; row < kAZT; row += kAZThreads / 32) {
+        const int zi = id.z0 + row;
+        const bool ok = zi < B.nz;
+        cp_async4(kb + row * 32 + col, B.ki + c0 + (long long)(ok ? zi : 0) * pplane, ok);
     }
 }
 
 template <int R, class S>
-__device__ __forceinline__ float2 az_read(const float2 *buf, int p, int i) {
-    constexpr int ROWS = kAZT + 2 * R;
-    if constexpr (AZSlab<S>::kArrays == 2) {
-        return buf[p * ROWS * 32 + i];
-    } else {
-        const uint2 w = reinterpret_cast<const uint2 *>(buf)[i];
-        return Store<S>::unpack2(p ? w.y : w.x);
-    }
-}
-
-template <int R, class S>
-__global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G, TapPairs t) {
+__global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G, TapPairs t) {
     constexpr int T = 2 * R + 1;
     constexpr int ROWS = kAZT + 2 * R;
     constexpr int WIN = kAZO + 2 * R;
-    constexpr int STAGE = AZSlab<S>::kArrays * ROWS * 32;  // float2 units
+    constexpr int STAGE = az_stage<R>();
     using V2 = typename Store<S>::V2;
-    extern __shared__ float2 slab[];  // [2 stages][arrays][ROWS][32]
+    extern __shared__ float2 slab[];  // [2 stages]{[ROWS][32] pairs, [kAZT][32] K*I~}
     const int total = __ldg(G.starts + G.nb);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int stage = 0;
     AZSlabId next{};
     if ((int)blockIdx.x < total) {
         next = az_slab_of(G, blockIdx.x);
-        az_issue<R, S>(G, next, slab);
+        az_issue<R>(G, next, slab);
     }
     cp_async_commit();
     for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
         const AZSlabId id = next;
         if (sl + (int)gridDim.x < total) {
             next = az_slab_of(G, sl + gridDim.x);
-            az_issue<R, S>(G, next, slab + (stage ^ 1) * STAGE);
+            az_issue<R>(G, next, slab + (stage ^ 1) * STAGE);
         }
         cp_async_commit();
         cp_async_wait1();
@@ -488,36 +475,31 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
         const int zb = warp * kAZO;
         if (x < B.nx) {
             const float l1 = B.lambda1, l2 = B.lambda2;
-            float f1[kAZO];
-            {
-                float2 w[WIN];
-#pragma unroll
-                for (int j = 0; j < WIN; ++j) w[j] = az_read<R, S>(buf, 0, (zb + j) * 32 + lane);
-#pragma unroll
-                for (int o = 0; o < kAZO; ++o) {
-                    float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
-                    f1[o] = __fdividef(acc.x, acc.y);
-                }
-            }
             float2 w[WIN];
 #pragma unroll
-            for (int j = 0; j < WIN; ++j) w[j] = az_read<R, S>(buf, 1, (zb + j) * 32 + lane);
+            for (int j = 0; j < WIN; ++j) w[j] = buf[(zb + j) * 32 + lane];
             const long long pplane = (long long)B.px * B.ny;
             const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
             V2 *ab = reinterpret_cast<V2 *>(B.ab) + off;
             float2 *abf = B.abxy + off;
+            const float *ki = reinterpret_cast<const float *>(buf + ROWS * 32) + zb * 32 + lane;
+            const float kxy = __ldg(B.prof + x) * __ldg(B.prof + B.nx + id.y);
+            const float *pz = B.prof + B.nx + B.ny + id.z0 + zb;
             float *const dump = B.dump;
 #pragma unroll
             for (int o = 0; o < kAZO; ++o) {
                 const int zo = id.z0 + zb + o;
                 if (zo < B.nz) {
-                    float2 acc = make_float2(0.f, 0.f);
+                    float2 acc = make_float2(0.f, 0.f);  // (K*(H I~), K*H)
 #pragma unroll
                     for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
-                    const float f2 = __fdividef(acc.x, acc.y);
-                    const float2 v = make_float2(l1 * f1[o] - l2 * f2, l1 * (f1[o] * f1[o]) - l2 * (f2 * f2));
+                    const float f1 = __fdividef(acc.x, acc.y);
+                    // K*(1-H) = K*1 - K*H keeps few significant bits once 1-H < ~1e-6 over the
+                    // whole window (phi > ~3e5 there, delta < 4e-12); the fit is then taken as
+                    // f1, the window mean in that limit, so that it stays finite
+                    const float k1 = kxy * __ldg(pz + o), den = k1 - acc.y;
+                    const float f2 = den > 0x1p-20f * k1 ? __fdividef(ki[o * 32] - acc.x, den) : f1;
+                    const float2 v = make_float2(l1 * f1 - l2 * f2, l1 * (f1 * f1) - l2 * (f2 * f2));
                     if (G.ab_f32)
                         abf[o * pplane] = v;
                     else
@@ -525,7 +507,7 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
                     if (dump) {
                         const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
                         const long long n = (long long)B.nx * B.ny * B.nz;
-                        dump[q] = f1[o] * B.cs[3] + B.cs[0];
+                        dump[q] = f1 * B.cs[3] + B.cs[0];
                         dump[n + q] = f2 * B.cs[3] + B.cs[0];
                     }
                 }
@@ -533,6 +515,49 @@ __global__ void __launch_bounds__(kAZThreads, R <= 8 ? 2 : 1) k_ta_z(GroupArgs G
         }
         __syncthreads();  // this stage is refilled by the next iteration's copies
         stage ^= 1;
+    }
+}
+
+// ------------------------------------------------------- set-up: K*I~
+
+// K*I~ of one brick, once per solve: the x/y kernel on (I~, 0) into b.abxy,
+// then a z convolution of its first component into b.ki.  Launched per brick
+// (the descriptor by value), on the x/y kernel's tiles and the slabs of group A.
+template <int R, class ImgT>
+__global__ void __launch_bounds__(kXYThreads) k_ki_xy(BrickDev B, TapPairs t) {
+    extern __shared__ float2 sm[];
+    const int ntx = (B.nx + kXYT - 1) / kXYT, nty = (B.ny + kXYT - 1) / kXYT;
+    const int tx = blockIdx.x % ntx, r = blockIdx.x / ntx;
+    ProI<ImgT> pro{reinterpret_cast<const ImgT *>(B.img), B.cs[1], -B.cs[0] * B.cs[1]};
+    OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
+    xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.nx, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes, t, sm);
+}
+
+template <int R>
+__global__ void __launch_bounds__(kAZThreads) k_ki_z(BrickDev B, TapPairs t) {
+    constexpr int T = 2 * R + 1;
+    constexpr int WIN = kAZO + 2 * R;
+    const int nzt = (B.nz + kAZT - 1) / kAZT, nxt = (B.nx + 31) / 32;
+    const int zt = blockIdx.x % nzt, rest = blockIdx.x / nzt;
+    const int x = (rest % nxt) * 32 + (threadIdx.x & 31), y = rest / nxt;
+    const int z0 = zt * kAZT + (threadIdx.x >> 5) * kAZO;
+    if (x >= B.nx) return;
+    const long long pplane = (long long)B.px * B.ny;
+    const float2 *src = B.abxy + (long long)y * B.px + x;
+    float w[WIN];
+#pragma unroll
+    for (int j = 0; j < WIN; ++j) {
+        const int zi = z0 - R + j;
+        w[j] = (unsigned)zi < (unsigned)B.nz ? __ldg(src + zi * pplane).x : 0.f;
+    }
+#pragma unroll
+    for (int o = 0; o < kAZO; ++o) {
+        if (z0 + o < B.nz) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < T; ++k) acc = fmaf(t.g[k].x, w[o + k], acc);
+            B.ki[(long long)(z0 + o) * pplane + (long long)y * B.px + x] = acc;
+        }
     }
 }
 
@@ -807,19 +832,19 @@ int &az_persist() {
 template <int R, class S>
 cudaError_t prepare_storage() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint8_t, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint16_t, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_ta_xy<R, float, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)XYLayout<R, 2>::bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_ta_z<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)az_smem<R, S>())) !=
+    if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)XYLayout<R, 1>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)XYLayout<R, 1>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_ta_xy<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)XYLayout<R, 1>::bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_ta_z<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)az_smem<R>())) !=
         cudaSuccess) return e;
     {
         int dev = 0, sms = 0, occ = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ta_z<R, S>, kAZThreads, az_smem<R, S>())) !=
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ta_z<R, S>, kAZThreads, az_smem<R>())) !=
             cudaSuccess) return e;
         az_persist<R, S>() = sms * (occ > 0 ? occ : 1);
     }
@@ -834,18 +859,18 @@ cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cuda
     {
         ProfScope ps(prof, KID_TA_XY);
         G.starts = g.starts[0];
-        constexpr size_t sm = XYLayout<R, 2>::bytes;
+        constexpr size_t sm = XYLayout<R, 1>::bytes;
         switch (g.imgtype) {
-            case 0: k_ta_xy<R, uint8_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
-            case 1: k_ta_xy<R, uint16_t, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
-            default: k_ta_xy<R, float, S><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp);
+            case 0: k_ta_xy<R, uint8_t><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
+            case 1: k_ta_xy<R, uint16_t><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
+            default: k_ta_xy<R, float><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp);
         }
     }
     {
         ProfScope ps(prof, KID_TA_Z);
         G.starts = g.starts[1];
         const unsigned grid = g.ncta[1] < (unsigned)az_persist<R, S>() ? g.ncta[1] : (unsigned)az_persist<R, S>();
-        k_ta_z<R, S><<<grid, kAZThreads, az_smem<R, S>(), s>>>(G, tp);
+        k_ta_z<R, S><<<grid, kAZThreads, az_smem<R>(), s>>>(G, tp);
     }
     if (!g.force) {  // the Eq. (15) form has no group-B convolutions
         ProfScope ps(prof, KID_TB_XY);

@@ -123,17 +123,55 @@ void tiled_cta_counts(const BrickDev &b, unsigned counts[4]) {
                 ((b.nz + b.zc - 1) / b.zc);
 }
 
+// Per pitched voxel: (H I~, H) 8 bytes, (a, b) 2 elements of the storage type,
+// x/y-convolved (a, b) 8 bytes, K*I~ 4 bytes (np is even: every view is 8-byte aligned).
 size_t tiled_stage_bytes(int storage, long long np) {
     const size_t e = storage == 0 ? 4 : 2;
-    return e * 4 * np + e * 2 * np + 8 * np;
+    return (8 + 2 * e + 8 + 4) * (size_t)np;
 }
 
-void tiled_stage_views(int storage, void *base, long long np, void **u4, void **ab, float2 **abxy) {
+void tiled_stage_views(int storage, void *base, long long np, float2 **u2, void **ab, float2 **abxy, float **ki) {
     const size_t e = storage == 0 ? 4 : 2;
     char *p = static_cast<char *>(base);
-    *u4 = p;
-    *ab = p + e * 4 * np;
-    *abxy = reinterpret_cast<float2 *>(p + e * 6 * np);
+    *u2 = reinterpret_cast<float2 *>(p);
+    *ab = p + 8 * np;
+    *abxy = reinterpret_cast<float2 *>(p + (8 + 2 * e) * np);
+    *ki = reinterpret_cast<float *>(p + (16 + 2 * e) * np);
+}
+
+namespace {
+template <int R, class ImgT>
+cudaError_t ki_init_r(const BrickDev &b, const Taps &taps, cudaStream_t s) {
+    static_assert(tiled::XYLayout<R, 1>::bytes <= 48 * 1024, "k_ki_xy needs no shared-memory opt-in");
+    const tiled::TapPairs tp = tiled::tap_pairs(taps);
+    unsigned counts[4];
+    tiled_cta_counts(b, counts);
+    tiled::k_ki_xy<R, ImgT><<<counts[0], tiled::kXYThreads, tiled::XYLayout<R, 1>::bytes, s>>>(b, tp);
+    tiled::k_ki_z<R><<<counts[1], tiled::kAZThreads, 0, s>>>(b, tp);
+    return cudaGetLastError();
+}
+template <int R>
+cudaError_t ki_init_i(const BrickDev &b, int imgtype, const Taps &taps, cudaStream_t s) {
+    switch (imgtype) {
+        case 0: return ki_init_r<R, uint8_t>(b, taps, s);
+        case 1: return ki_init_r<R, uint16_t>(b, taps, s);
+        default: return ki_init_r<R, float>(b, taps, s);
+    }
+}
+}  // namespace
+
+cudaError_t tiled_ki_init(const BrickDev &b, int imgtype, const Taps &taps, cudaStream_t s) {
+    switch (taps.R) {
+        case 2: return ki_init_i<2>(b, imgtype, taps, s);
+        case 3: return ki_init_i<3>(b, imgtype, taps, s);
+        case 4: return ki_init_i<4>(b, imgtype, taps, s);
+        case 5: return ki_init_i<5>(b, imgtype, taps, s);
+        case 6: return ki_init_i<6>(b, imgtype, taps, s);
+        case 8: return ki_init_i<8>(b, imgtype, taps, s);
+        case 10: return ki_init_i<10>(b, imgtype, taps, s);
+        case 12: return ki_init_i<12>(b, imgtype, taps, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace rsf

@@ -14,7 +14,7 @@ import pytest
 import oracle
 from paper_2404_02813_gb300 import rsf, synth
 
-from _parity import assert_phi_close, paper_c1, storage_force_tol
+from _parity import assert_phi_close, fits_force_tol, paper_c1, storage_force_tol
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,7 +57,9 @@ def ectx(request):
 
 def _check(ctx, vol, phi_n, nxt, p, what):
     ref, dump = oracle.step(_f64(vol), _f64(phi_n), p, dump=True, omp=True, force="eq15")
-    force = None if ctx.storage == "f32" else storage_force_tol(phi_n, dump, p, UNIT[ctx.storage])
+    force = fits_force_tol(vol, phi_n, dump, p)
+    if ctx.storage != "f32":
+        force = force + storage_force_tol(phi_n, dump, p, UNIT[ctx.storage])
     err = assert_phi_close(nxt, ref, phi_n, rel=REL[ctx.storage], force=force, sign_max=SIGN[ctx.storage],
                            what=f"eq15 {ctx.storage} {what}")
     print(f"eq15 {ctx.storage} {what}: max |dphi| {err:.3e}, sign disagreement "
