@@ -753,6 +753,8 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     for (int s = 0; s < 2 * R + 2; ++s) ring[s] = load(s);
     float iv0 = active ? centred(img, (long long)z0 * plane, inv_s, nms) : 0.f;
     float iv1 = (active && nout > 1) ? centred(img, (long long)(z0 + 1) * plane, inv_s, nms) : 0.f;
+    // p_z of the step's two planes, loaded a step ahead like the image
+    float kz0 = R == 0 ? 1.f : __ldg(profz), kz1 = R == 0 || nout < 2 ? 1.f : __ldg(profz + 1);
 
     for (int base = 0; 2 * base < nout; base += SPB) {
 #pragma unroll
@@ -768,9 +770,11 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
                 store_phi(phi_at(2 * kk + 5), pvb);
                 fetch_phi(zo + 6, pva);
                 fetch_phi(zo + 7, pvb);
-                const float im0 = iv0, im1 = iv1;
+                const float im0 = iv0, im1 = iv1, pz0 = kz0, pz1 = kz1;
                 if (active && r0 + 2 < nout) iv0 = centred(img, (long long)(zo + 2) * plane, inv_s, nms);
                 if (active && r0 + 3 < nout) iv1 = centred(img, (long long)(zo + 3) * plane, inv_s, nms);
+                if (R != 0 && r0 + 2 < nout) kz0 = __ldg(profz + r0 + 2);
+                if (R != 0 && r0 + 3 < nout) kz1 = __ldg(profz + r0 + 3);
                 __syncthreads();
 #pragma unroll
                 for (int c = 3; c <= 4; ++c) {
@@ -787,7 +791,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
 #pragma unroll
                         for (int kt = 0; kt < T; ++kt) acc = f2fma(t.g[kt], ring[(2 * kk + c + kt) % M], acc);
                         const float im = c ? im1 : im0;
-                        const float K1 = R == 0 ? 1.f : pxy * __ldg(profz + r0 + c);
+                        const float K1 = R == 0 ? 1.f : pxy * (c ? pz1 : pz0);
                         const float g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
                         const float *p0 = phi_at(2 * kk + c);
                         const int pc0 = (ty + 2) * PW + tx + 2;
