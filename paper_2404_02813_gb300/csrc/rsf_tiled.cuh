@@ -208,8 +208,8 @@ struct XYLayout {
     static constexpr size_t bytes = sizeof(float2) * (IN + XC);
 };
 
-template <int R, int NP>
-constexpr int xy_min_blocks() { return R <= 6 ? 3 : 2; }
+// Resident CTAs per SM the x/y kernels are compiled for: 3 (4 for rsf_ta_xy at
+// radius <= 6) measured faster than 2 at radii 8-12 in spite of a few spilled words.
 
 // The x/y kernel body for one CTA of one brick: planes [za, za + kXYPlanes) of
 // tile (x0, y0).  The global loads of plane z+1 are issued right after the
@@ -346,7 +346,7 @@ __device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev 
 }
 
 template <int R, class ImgT>
-__global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 2) k_ta_xy(GroupArgs G, TapPairs t) {
+__global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 3) k_ta_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
     const BrickDev B = G.bricks[b];
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 2) k_ta_xy(GroupArgs 
 }
 
 template <int R, class S>
-__global__ void __launch_bounds__(kXYThreads, xy_min_blocks<R, 1>()) k_tb_xy(GroupArgs G, TapPairs t) {
+__global__ void __launch_bounds__(kXYThreads, 3) k_tb_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
     const BrickDev B = G.bricks[b];
