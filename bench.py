@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 # Algorithmic HBM bytes per voxel and launch of each per-iteration kernel: the
 # fields it must read once and write once, independent of tiling.  `img` is the
 # image's byte size (the tiled kernels read it in its own type), `st` the
-# storage byte size of the group-A fields and (a, b) (4, or 2 for FP16/BF16).
+# storage byte size of (a, b) (4, or 2 for FP16/BF16).
 def algo_bytes_per_voxel(img: int, st: int, force: str = "li") -> dict:
     # the Eq. (15) form writes (a, b) in FP32 from rsf_ta_z and has no rsf_tb_xy
     ab_out = 8 if force == "eq15" else 2 * st

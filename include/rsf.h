@@ -245,13 +245,14 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *   RSF_OPT_ZCHUNK  z planes per CTA of the z-marching kernel; 0 (default)
  *                   picks enough chunks for about 16 CTAs per SM; else >= 8.
  *                   Results do not depend on it.
- *   RSF_OPT_STORAGE rsf_storage of the tiled path's intermediate fields: the
- *                   four group-A fields (K*(H I), K*H, K*((1-H) I), K*(1-H)
- *                   after the x and y passes) and the fits' combinations
- *                   a, b; RSF_STORE_F32 (default), RSF_STORE_BF16 or
- *                   RSF_STORE_F16.  Accumulation is FP32 throughout; phi, the
- *                   image (read in its own type) and the x/y-convolved a, b
- *                   stay exact / FP32.  16-bit storage needs the tiled path.
+ *   RSF_OPT_STORAGE rsf_storage of the tiled path's stored fits'
+ *                   combinations a, b; RSF_STORE_F32 (default), RSF_STORE_BF16
+ *                   or RSF_STORE_F16.  Accumulation is FP32 throughout; phi,
+ *                   the image (read in its own type), the x/y-convolved pair
+ *                   (H I, H), K*I and the x/y-convolved a, b stay exact /
+ *                   FP32 (group A forms K*((1-H) I) and K*(1-H) as
+ *                   differences, which 16-bit storage would not survive).
+ *                   16-bit storage needs the tiled path.
  *   RSF_OPT_AUTOTUNE 1: rsf_evolve_batch picks the update kernel's z chunk per
  *                   brick group by timing candidates on a discarded first
  *                   iteration and remembers the choice in the context; 0

@@ -1,5 +1,5 @@
 // rsf_tiled_f16.cu -- instantiates the tiled iteration with FP16 storage of
-// the group-A fields and of (a, b) (see rsf_tiled.cuh).
+// (a, b) (see rsf_tiled.cuh).
 #include "rsf_tiled.cuh"
 
 namespace rsf {

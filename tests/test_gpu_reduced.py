@@ -1,7 +1,7 @@
 """16-bit storage of the intermediate fields (FP16, BF16) against the FP64 oracle.
 
-The group-A fields and (a, b) are stored in 16 bits with FP32 accumulation;
-phi, the image and the x/y-convolved (a, b) stay exact / FP32.  The gate is
+(a, b) are stored in 16 bits with FP32 accumulation; phi, the image, the
+x/y-convolved group-A pair, K*I and the x/y-convolved (a, b) stay exact / FP32.  The gate is
 the per-iteration bound for reduced storage: 2e-2 * c0, plus eight FP32 ulps of
 |phi|, plus four unit roundoffs of the storage format (2^-11 for FP16) times the
 non-cancelled size of the force, dt * delta(phi_n) * (l1 |e1| + l2 |e2|): the
