@@ -60,10 +60,21 @@ PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
 NCU_TRAFFIC = {
-    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "d7ecee287d7f37a9",
+    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "149364b79e1a1caf",
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
-    for k, v in {"rsf_ta_xy": 13.40, "rsf_ta_z": 19.34, "rsf_tb_xy": 15.26, "rsf_tb_z": 21.95}.items()
+    for k, v in {"rsf_ta_xy": 13.39, "rsf_ta_z": 19.34, "rsf_tb_xy": 15.28, "rsf_tb_z": 21.98}.items()
 }
+
+# Issue slots per voxel measured by ncu (smsp__inst_executed.sum * 32 / voxels: warp
+# instructions, counted per thread lane), same capture conditions and gating as
+# NCU_TRAFFIC.  The kernels are issue-bound; against one warp instruction per
+# cycle per SM sub-partition (4 per SM) this gives the issue roofline.
+NCU_INST = {
+    k: {"inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "149364b79e1a1caf",
+        "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage"}
+    for k, v in {"rsf_ta_xy": 131.3, "rsf_ta_z": 128.1, "rsf_tb_xy": 96.0, "rsf_tb_z": 253.4}.items()
+}
+SM_SUBPARTITIONS = 4  # warp schedulers per SM, one warp instruction issued per cycle each
 
 P_LIGHTSHEET = 4300.0
 
@@ -324,7 +335,7 @@ def run_batch(args, rank, world, local):
                          "note": "per-kernel times from one extra step with per-launch events"},
             "kernels": {k: {"launches": n, "ms": round(m, 3)} for k, (n, m) in prof.items() if n},
             "clocks": clk,
-            "gpu_launches": (4 * iters + 4 * nb) * args.steps,
+            "gpu_launches": (4 * iters + 5 * nb) * args.steps,  # per brick set-up: statistics (2), q, K*I~ (2)
             "e2e": e2e,
         }
         if world == 1 and not args.no_cpu_baseline:
@@ -743,6 +754,18 @@ def main():
         same_case = args.storage == "f32" and vol.dtype == np.uint16 and params["sigma"] == 3.0 and force == "li"
         traffic = (tr["bytes_per_voxel"] * n_vox
                    if tr and same_case and tr.get("source_sha") == _source_sha(tr.get("source", "")) else None)
+        issue = None
+        ti = NCU_INST.get(dom)
+        if ti and same_case and ti.get("source_sha") == _source_sha(ti.get("source", "")):
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
+            ach = ti["inst_per_voxel"] / 32.0 * n_vox / avg_s
+            pk = sms * SM_SUBPARTITIONS * mhz * 1e6
+            issue = {"kernel": dom, "warp_inst_per_voxel": ti["inst_per_voxel"] / 32.0,
+                     "achieved_warp_inst_s": ach, "peak_warp_inst_s": pk, "frac": ach / pk, "sm_mhz": mhz,
+                     "note": "instruction issue roofline of the dominant kernel: ncu-counted warp instructions "
+                             "per voxel x voxels / CUDA-event launch time, against one issue per cycle per SM "
+                             "sub-partition at the sampled SM clock"}
         launches = sum(n for n, _ in prof.values()) + (SETUP_LAUNCHES * args.steps if not args.curtain
                                                        else (7 * nbox + 1) * args.steps)
         line = {
@@ -772,6 +795,8 @@ def main():
             "gpu_launches": launches,
             "e2e": e2e,
         }
+        if issue is not None:
+            line["issue_roofline"] = issue
         if vs_fp32 is not None:
             line["vs_fp32"] = vs_fp32
         if seg is not None:
