@@ -211,49 +211,41 @@ struct XYLayout {
 // Resident CTAs per SM the x/y kernels are compiled for: 3 (4 for rsf_ta_xy at
 // radius <= 6) measured faster than 2 at radii 8-12 in spite of a few spilled words.
 
-// The x/y kernel body for one CTA of one brick: planes [za, za + kXYPlanes) of
-// tile (x0, y0).  The global loads of plane z+1 are issued right after the
-// first barrier of plane z and land in registers while the convolutions run.
-// Input row pitch `ipx`; output pitch `opx`; `Out` writes the NP pairs.
-template <int R, int NP, class Pro, class Out>
-__device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, int ny, int nz, int ipx, int x0,
-                                        int y0, int za, const TapPairs &t, float2 *sm) {
+// Loads the x/y kernel's input tile of one plane entry by entry (any row
+// pitch): entry e of this thread has its offset within the plane (-1 outside
+// the brick) and its shared-memory index; entries e < NFULL always lie inside
+// the tile.  fetch(z) issues the global loads of plane z into registers,
+// store(in) writes the NP pairs into the tile.
+template <int R, int NP, class Pro>
+struct ScalarLoader {
     using L = XYLayout<R, NP>;
     using Raw = typename Pro::Raw;
-    constexpr int T = 2 * R + 1;
-    constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
-    constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
-    constexpr int NE = (L::H * L::W + kXYThreads - 1) / kXYThreads;  // tile entries per thread
+    static constexpr int NE = (L::H * L::W + kXYThreads - 1) / kXYThreads;
+    static constexpr int NFULL = L::H * L::W / kXYThreads;
     static_assert(NE <= 32, "too many tile entries per thread");
-    float2 *in = sm;
-    float2 *xc = sm + L::IN;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int zb_end = min(za + kXYPlanes, nz);
-    const long long iplane = (long long)ipx * ny;
-
-    // tile entry e of this thread: offset within the plane (-1 outside the brick)
-    // and shared-memory index; entries e < NFULL always lie inside the tile
-    constexpr int NFULL = L::H * L::W / kXYThreads;
+    const Pro &pro;
+    long long iplane;
     int eoff[NE], esm[NE];
-#pragma unroll
-    for (int e = 0; e < NE; ++e) {
-        const int i = threadIdx.x + e * kXYThreads;
-        const int ii = min(i, L::H * L::W - 1);
-        const int ly = ii / L::W, lx = ii - ly * L::W;
-        const int gx = x0 + lx - R, gy = y0 + ly - R;
-        const bool in_vol = i < L::H * L::W && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-        eoff[e] = in_vol ? gy * ipx + gx : -1;
-        esm[e] = i < L::H * L::W ? ly * L::P + lx : -1;
-    }
     Raw raw[NE];
-    auto fetch = [&](int z) {
+    __device__ __forceinline__ ScalarLoader(const Pro &p, int nx, int ny, int ipx, int x0, int y0)
+        : pro(p), iplane((long long)ipx * ny) {
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int i = threadIdx.x + e * kXYThreads;
+            const int ii = min(i, L::H * L::W - 1);
+            const int ly = ii / L::W, lx = ii - ly * L::W;
+            const int gx = x0 + lx - R, gy = y0 + ly - R;
+            const bool in_vol = i < L::H * L::W && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+            eoff[e] = in_vol ? gy * ipx + gx : -1;
+            esm[e] = i < L::H * L::W ? ly * L::P + lx : -1;
+        }
+    }
+    __device__ __forceinline__ void fetch(int z) {
         const auto pl = pro.plane((long long)z * iplane);
 #pragma unroll
         for (int e = 0; e < NE; ++e) raw[e] = eoff[e] >= 0 ? pro.fetch(pl, eoff[e]) : pro.zero();
-    };
-    fetch(za);
-    for (int z = za; z < zb_end; ++z) {
+    }
+    __device__ __forceinline__ void store(float2 *in) const {
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
             if (e < NFULL || esm[e] >= 0) {
@@ -263,8 +255,109 @@ __device__ __forceinline__ void xy_tile(const Pro &pro, const Out &out, int nx, 
                 for (int p = 0; p < NP; ++p) in[p * L::H * L::P + esm[e]] = v[p];
             }
         }
+    }
+};
+
+// The same tile of (H I~, H) loaded four columns at a time: one 16-byte load
+// of q and one load of four image values per group, window columns
+// [x0 - RA, x0 + 32 + RA) with RA = R rounded up to a multiple of 4.  Needs an
+// even R <= 8 (used for R <= 6) and a row pitch (= nx) that is a multiple of 4, so that a group
+// lies wholly inside or wholly outside the brick and its pairs of columns are
+// 16-byte aligned in the tile (two 16-byte shared stores per group).
+template <class T> struct Vec4;
+template <> struct Vec4<uint8_t> { using V = uchar4; };
+template <> struct Vec4<uint16_t> { using V = ushort4; };
+template <> struct Vec4<float> { using V = float4; };
+
+template <int R, class ImgT>
+struct VecLoaderH {
+    using L = XYLayout<R, 1>;
+    static_assert(R % 2 == 0 && R <= 8, "even radius <= 8");
+    static constexpr int RA = (R + 3) / 4 * 4;
+    static constexpr int NG = (32 + 2 * RA) / 4;                       // groups per row
+    static constexpr int NV = (L::H * NG + kXYThreads - 1) / kXYThreads;  // groups per thread
+    using V = typename Vec4<ImgT>::V;
+    const float *q;
+    const ImgT *img;
+    float inv_s, nms;
+    long long iplane;
+    int goff[NV];  // group offset in the plane (-1: outside the brick)
+    int sm0[NV];   // tile index of the group's first column (may lie left of the tile)
+    int lx0[NV];   // tile column of the group's first column; kNone: no group for this thread
+    static constexpr int kNone = -1 << 20;
+    float4 rq[NV];
+    V ri[NV];
+    __device__ __forceinline__ VecLoaderH(const float *q_, const ImgT *img_, float inv_s_, float nms_, int nx, int ny,
+                                          int x0, int y0)
+        : q(q_), img(img_), inv_s(inv_s_), nms(nms_), iplane((long long)nx * ny) {
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            const int i = threadIdx.x + e * kXYThreads;
+            const int ii = min(i, L::H * NG - 1);
+            const int row = ii / NG, g = ii - row * NG;
+            const int gy = y0 + row - R, gx = x0 - RA + 4 * g;
+            const bool in_vol = i < L::H * NG && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+            goff[e] = in_vol ? gy * nx + gx : -1;
+            sm0[e] = row * L::P + 4 * g - RA + R;
+            lx0[e] = i < L::H * NG ? 4 * g - RA + R : kNone;
+        }
+    }
+    __device__ __forceinline__ void fetch(int z) {
+        const float *qp = q + (long long)z * iplane;
+        const ImgT *ip = img + (long long)z * iplane;
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            if (goff[e] >= 0) {
+                rq[e] = __ldg(reinterpret_cast<const float4 *>(qp + goff[e]));
+                ri[e] = __ldg(reinterpret_cast<const V *>(ip + goff[e]));
+            } else {
+                rq[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ri[e] = V{};
+            }
+        }
+    }
+    __device__ __forceinline__ float2 pair(float qv, float iv, bool inside) const {
+        const float h = h_of_q(qv);
+        return inside ? make_float2(h * fmaf(iv, inv_s, nms), h) : make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void store(float2 *in) const {
+#pragma unroll
+        for (int e = 0; e < NV; ++e) {
+            const int c0 = sm0[e], lx = lx0[e];
+            const bool inside = goff[e] >= 0;
+            if (lx >= 0 && lx + 1 < L::W) {
+                const float2 a = pair(rq[e].x, (float)ri[e].x, inside), b = pair(rq[e].y, (float)ri[e].y, inside);
+                *reinterpret_cast<float4 *>(in + c0) = make_float4(a.x, a.y, b.x, b.y);
+            }
+            if (lx != kNone && lx + 2 >= 0 && lx + 3 < L::W) {
+                const float2 a = pair(rq[e].z, (float)ri[e].z, inside), b = pair(rq[e].w, (float)ri[e].w, inside);
+                *reinterpret_cast<float4 *>(in + c0 + 2) = make_float4(a.x, a.y, b.x, b.y);
+            }
+        }
+    }
+};
+
+// The x/y kernel body for one CTA of one brick: planes [za, za + kXYPlanes) of
+// tile (x0, y0).  The global loads of plane z+1 are issued right after the
+// first barrier of plane z and land in registers while the convolutions run.
+// `Out` writes the NP pairs (pitch out.px).
+template <int R, int NP, class Loader, class Out>
+__device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int ny, int nz, int x0, int y0, int za,
+                                        const TapPairs &t, float2 *sm) {
+    using L = XYLayout<R, NP>;
+    constexpr int T = 2 * R + 1;
+    constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
+    constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
+    float2 *in = sm;
+    float2 *xc = sm + L::IN;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int zb_end = min(za + kXYPlanes, nz);
+    ld.fetch(za);
+    for (int z = za; z < zb_end; ++z) {
+        ld.store(in);
         __syncthreads();
-        if (z + 1 < zb_end) fetch(z + 1);
+        if (z + 1 < zb_end) ld.fetch(z + 1);
         {
             const int h = lane >> 4, r = (lane >> 2) & 3, g = lane & 3;
             for (int item = warp; item < NP * NRB * 2; item += kXYThreads / 32) {
@@ -352,9 +445,22 @@ __global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 3) k_ta_xy(GroupArgs 
     const BrickDev B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
-    ProH<ImgT> pro{(G.parity ^ B.flip) ? B.q[1] : B.q[0], reinterpret_cast<const ImgT *>(B.img), inv_s, nms};
+    const float *q = (G.parity ^ B.flip) ? B.q[1] : B.q[0];
+    const ImgT *img = reinterpret_cast<const ImgT *>(B.img);
     OutF2 out{B.u2, B.px, (long long)B.px * B.ny};
-    xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.nx, tl.x0, tl.y0, tl.za, t, sm);
+    if constexpr (R % 2 == 0 && R <= 6) {
+        // four columns per load where the row pitch and both base addresses allow it (uniform per CTA);
+        // at radius 8 the second code path cost more registers than the loads saved (measured)
+        if (B.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0 &&
+            reinterpret_cast<uintptr_t>(img) % (4 * sizeof(ImgT)) == 0) {
+            VecLoaderH<R, ImgT> ld(q, img, inv_s, nms, B.nx, B.ny, tl.x0, tl.y0);
+            xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
+            return;
+        }
+    }
+    ProH<ImgT> pro{q, img, inv_s, nms};
+    ScalarLoader<R, 1, ProH<ImgT>> ld(pro, B.nx, B.ny, B.nx, tl.x0, tl.y0);
+    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
 }
 
 template <int R, class S>
@@ -365,7 +471,8 @@ __global__ void __launch_bounds__(kXYThreads, 3) k_tb_xy(GroupArgs G, TapPairs t
     const XYTile tl = xy_tile_of(G, B, b);
     ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
-    xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.px, tl.x0, tl.y0, tl.za, t, sm);
+    ScalarLoader<R, 1, ProAB<S>> ld(pro, B.nx, B.ny, B.px, tl.x0, tl.y0);
+    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
 }
 
 // ------------------------------------------------------------------ A: z
@@ -530,7 +637,8 @@ __global__ void __launch_bounds__(kXYThreads) k_ki_xy(BrickDev B, TapPairs t) {
     const int tx = blockIdx.x % ntx, r = blockIdx.x / ntx;
     ProI<ImgT> pro{reinterpret_cast<const ImgT *>(B.img), B.cs[1], -B.cs[0] * B.cs[1]};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
-    xy_tile<R, 1>(pro, out, B.nx, B.ny, B.nz, B.nx, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes, t, sm);
+    ScalarLoader<R, 1, ProI<ImgT>> ld(pro, B.nx, B.ny, B.nx, tx * kXYT, (r % nty) * kXYT);
+    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes, t, sm);
 }
 
 template <int R>
