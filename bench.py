@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -60,7 +61,7 @@ PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
 NCU_TRAFFIC = {
-    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "d14305ee12afce40",
+    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "69c363a2c15835db",
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
     for k, v in {"rsf_ta_xy": 13.30, "rsf_ta_z": 19.33, "rsf_tb_xy": 15.27, "rsf_tb_z": 21.96}.items()
 }
@@ -70,7 +71,7 @@ NCU_TRAFFIC = {
 # NCU_TRAFFIC.  The kernels are issue-bound; against one warp instruction per
 # cycle per SM sub-partition (4 per SM) this gives the issue roofline.
 NCU_INST = {
-    k: {"inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "d14305ee12afce40",
+    k: {"inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "69c363a2c15835db",
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage"}
     for k, v in {"rsf_ta_xy": 121.9, "rsf_ta_z": 128.1, "rsf_tb_xy": 96.0, "rsf_tb_z": 253.4}.items()
 }
@@ -80,8 +81,16 @@ P_LIGHTSHEET = 4300.0
 
 
 def _source_sha(fname: str) -> str:
+    """SHA-256 prefix of a kernel source with its comments and blank space removed, so
+    that the ncu figures stay attached to the code they were measured on."""
     p = os.path.join(ROOT, "paper_2404_02813_gb300", "csrc", fname)
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else ""
+    if not os.path.exists(p):
+        return ""
+    text = open(p, encoding="utf-8").read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = " ".join(text.split())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def peaks():

@@ -9,8 +9,9 @@
 //
 //   rsf_ta_xy  per z-plane, a 32x32 output tile plus an R halo in shared
 //              memory: forms H I~ and H (Eqs. 6, 8-10) from the image
-//              (centred on load) and q = +-atan(eps/|phi|)/pi, convolves the
-//              pair along x then y (packed f32x2 FMAs) and stores it (FP32).
+//              (centred on load; four columns per load where alignment
+//              allows) and q = +-atan(eps/|phi|)/pi, convolves the pair along
+//              x then y (packed f32x2 FMAs) and stores it (FP32).
 //   rsf_ta_z   x-z slabs (32 columns x 64 output planes) staged in shared
 //              memory by cp.async, two slabs in flight; z convolution over a
 //              register window; the local fits f1 = K*(H I~)/K*H and
@@ -23,7 +24,7 @@
 //              below is a difference of terms much larger than itself).
 //   rsf_tb_z   a z march over a 32x8 column tile: a register ring of (a, b)
 //              planes, a phi ring and a unit-normal ring in shared memory
-//              (each normal computed once per voxel);
+//              (each normal computed once per tile position, not per use);
 //              g = s^2 [ (l1 - l2) K1 I~^2 - 2 I~ K*a + K*b ]  (Eqs. 11-12),
 //              kappa and the Laplacian (Eqs. 3-4), the update of Eqs. (1),
 //              (13), (14), and q of the new phi for the next rsf_ta_xy.
