@@ -45,6 +45,7 @@ typedef struct rsf_ctx rsf_ctx; /* opaque; one per device */
 typedef int32_t rsf_status;
 #define RSF_OK 0
 #define RSF_PENDING 1
+#define RSF_SUSPENDED 2      /* final status of a suspended serving request (rsf_suspend) */
 #define RSF_E_INVAL (-1)     /* bad argument: null pointer, dim < 4, NaN or non-positive sigma/eps/dt, iters < 0 */
 #define RSF_E_NOMEM (-2)     /* the HBM budget or a device allocation was exceeded */
 #define RSF_E_CUDA (-3)      /* a CUDA runtime call failed; see rsf_last_error() */
@@ -320,13 +321,23 @@ rsf_status rsf_set_option(rsf_ctx *ctx, int32_t key, int64_t value);
  * alone exceeds the HBM budget), RSF_E_BUSY (queue full).
  *
  * rsf_poll returns RSF_PENDING, or the request's final status (RSF_OK,
- * RSF_E_CANCELLED, RSF_E_NOMEM, RSF_E_CUDA) together with its latency from
+ * RSF_SUSPENDED, RSF_E_CANCELLED, RSF_E_NOMEM, RSF_E_CUDA) together with its latency from
  * submission to completion in seconds (nullable); a ticket is released by the
  * first poll that returns a final status (later polls: RSF_E_NOTFOUND).
  * rsf_wait blocks up to timeout_ms (< 0: no limit) for a final status, then
  * behaves as rsf_poll; on expiry it returns RSF_E_TIMEOUT and keeps the ticket.
  * rsf_cancel marks a request cancelled: it leaves the queue, or the batch at
  * the next step, and its phi_out is not written.
+ * rsf_suspend marks a request for suspension (checkpointing): it leaves the
+ * queue, or the batch after its current step; phi_out receives phi after the
+ * iterations it completed (phi0 itself if none), their count is written to
+ * *iters_done (host memory, nullable, valid until the ticket resolves), and
+ * the final status is RSF_SUSPENDED.  phi and the iteration count are the
+ * whole state of the method: submitting phi_out with the remaining
+ * iterations (same volume, parameters, storage and form) resumes it, and the
+ * result equals the uninterrupted one bit for bit.  A request that finishes
+ * its iterations in the same step ends with RSF_OK instead.  Errors:
+ * RSF_E_NOTFOUND (unknown or already resolved ticket).
  * rsf_serve_stats reports counts, completed voxel-iterations, the busy time
  * from the first submission to the last completion, and latency percentiles
  * of the completed requests.
@@ -349,12 +360,14 @@ typedef struct {
     double voxel_iterations;
     double busy_s;
     double latency_p50_s, latency_p99_s, latency_max_s;
+    uint64_t suspended;
 } rsf_serve_stat;
 
 rsf_status rsf_submit(rsf_ctx *ctx, const rsf_request *req, uint64_t *ticket);
 rsf_status rsf_poll(rsf_ctx *ctx, uint64_t ticket, double *latency_s);
 rsf_status rsf_wait(rsf_ctx *ctx, uint64_t ticket, int32_t timeout_ms);
 rsf_status rsf_cancel(rsf_ctx *ctx, uint64_t ticket);
+rsf_status rsf_suspend(rsf_ctx *ctx, uint64_t ticket, int32_t *iters_done);
 rsf_status rsf_serve_stats(rsf_ctx *ctx, rsf_serve_stat *out);
 
 /*

@@ -11,7 +11,8 @@
 // bricks sharing a kernel radius, image type, storage and force form (the batched kernels
 // of rsf_evolve_batch); a brick admitted at tick T0 runs its iteration k at
 // tick T0 + k (its buffer parity is flipped accordingly).  A brick that has
-// done its iterations (or was cancelled) retires at once: its phi is copied to
+// done its iterations (or was cancelled, or suspended after its current
+// iteration) retires at once: its phi is copied to
 // the caller's phi_out, a host callback stamps its completion time, and its
 // memory returns to the pool in stream order, so the next admission can use
 // it.  The loop runs at most a few ticks ahead of the GPU.
@@ -61,6 +62,8 @@ struct Request {
     double t_submit = 0.0;
     std::atomic<int> status{RSF_PENDING};
     std::atomic<bool> cancel{false};
+    std::atomic<bool> suspend{false};
+    int32_t *iters_out = nullptr;  // where a suspension reports its completed iterations (under mu)
     double t_done = 0.0;
     // set at admission
     rsf::BrickDev d{};
@@ -102,7 +105,7 @@ struct Server {
     DescBuffers desc;
     int sms = 0;
     // statistics (mu)
-    uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, admitted = 0;
+    uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, suspended = 0, admitted = 0;
     double vox_iters = 0.0, t_first = 0.0, t_last = 0.0;
     std::vector<double> latencies;
     // host-side fault injection: the k-th admission (1-based) fails its set-up
@@ -116,8 +119,13 @@ void CUDART_CB done_cb(void *p) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         a->r->t_done = now_s();
+        if (a->status == RSF_SUSPENDED && a->r->iters_out) *a->r->iters_out = a->r->done_iters;
         a->r->status.store(a->status);
-        if (a->status == RSF_OK) {
+        if (a->status == RSF_SUSPENDED) {
+            ++s->suspended;
+            s->vox_iters += (double)a->r->n * a->r->done_iters;
+            s->t_last = a->r->t_done;
+        } else if (a->status == RSF_OK) {
             ++s->completed;
             s->latencies.push_back(a->r->t_done - a->r->t_submit);
             s->vox_iters += (double)a->r->n * a->r->req.iters;
@@ -255,14 +263,15 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     return true;
 }
 
-// Retire an active request after its last launch: copy out (unless cancelled),
-// stamp completion, return its memory in stream order.
-void retire(Server *s, const std::shared_ptr<Request> &r, bool cancelled) {
+// Retire an active request after its last launch: copy out (unless cancelled;
+// a suspended request copies phi after its done_iters iterations, the buffer of
+// that parity), stamp completion, return its memory in stream order.
+void retire(Server *s, const std::shared_ptr<Request> &r, bool cancelled, bool suspended = false) {
     rsf_ctx *c = s->ctx;
-    int st = RSF_OK;
+    int st = suspended ? RSF_SUSPENDED : RSF_OK;
     if (cancelled) {
         st = RSF_E_CANCELLED;
-    } else if (xfer(r->req.phi_out, r->d.phi[r->req.iters & 1], sizeof(float) * r->n, s->s_comp) != cudaSuccess) {
+    } else if (xfer(r->req.phi_out, r->d.phi[r->done_iters & 1], sizeof(float) * r->n, s->s_comp) != cudaSuccess) {
         st = RSF_E_CUDA;
     }
     cudaLaunchHostFunc(s->s_comp, done_cb, new DoneArg{s, r, st});
@@ -327,6 +336,17 @@ void loop(Server *s) {
                     lk.lock();
                     continue;
                 }
+                if (r->suspend.load()) {  // suspended before admission: its state is phi0, 0 iterations
+                    s->queue.pop_front();
+                    lk.unlock();
+                    r->done_iters = 0;
+                    cudaError_t e = xfer(r->req.phi_out, r->req.phi0, sizeof(float) * r->req.nx * r->req.ny * r->req.nz,
+                                         s->s_setup);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(s->s_setup);
+                    finish_now(s, r, e == cudaSuccess ? RSF_SUSPENDED : RSF_E_CUDA);
+                    lk.lock();
+                    continue;
+                }
                 const size_t need = footprint(r->req, !on_device(r->req.volume));
                 uint64_t used, budget;
                 {
@@ -363,8 +383,10 @@ void loop(Server *s) {
         for (auto &r : s->active) {
             ++r->done_iters;
             const bool cancelled = r->cancel.load();
-            if (cancelled || r->done_iters >= r->req.iters) {
-                retire(s, r, cancelled);
+            const bool finished = r->done_iters >= r->req.iters;
+            const bool suspended = !cancelled && !finished && r->suspend.load();
+            if (cancelled || finished || suspended) {
+                retire(s, r, cancelled, suspended);
                 s->groups_dirty = true;
             } else {
                 keep.push_back(r);
@@ -527,6 +549,19 @@ extern "C" rsf_status rsf_cancel(rsf_ctx *c, uint64_t ticket) {
     return RSF_OK;
 }
 
+extern "C" rsf_status rsf_suspend(rsf_ctx *c, uint64_t ticket, int32_t *iters_done) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    Server *s = static_cast<Server *>(c->server);
+    if (!s) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return fail(RSF_E_NOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    it->second->iters_out = iters_done;
+    it->second->suspend.store(true);
+    s->cv.notify_all();
+    return RSF_OK;
+}
+
 extern "C" rsf_status rsf_serve_stats(rsf_ctx *c, rsf_serve_stat *out) {
     if (!c || !out) return fail(RSF_E_INVAL, "null context or output");
     memset(out, 0, sizeof *out);
@@ -537,6 +572,7 @@ extern "C" rsf_status rsf_serve_stats(rsf_ctx *c, rsf_serve_stat *out) {
     out->completed = s->completed;
     out->failed = s->failed;
     out->cancelled = s->cancelled;
+    out->suspended = s->suspended;
     out->queued = s->queue.size();
     out->voxel_iterations = s->vox_iters;
     out->busy_s = s->t_last > s->t_first ? s->t_last - s->t_first : 0.0;

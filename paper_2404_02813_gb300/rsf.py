@@ -18,8 +18,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librsf.so")
 
-RSF_OK, RSF_PENDING = 0, 1
-STATUS_NAMES = {0: "RSF_OK", 1: "RSF_PENDING", -1: "RSF_E_INVAL", -2: "RSF_E_NOMEM", -3: "RSF_E_CUDA",
+RSF_OK, RSF_PENDING, RSF_SUSPENDED = 0, 1, 2
+STATUS_NAMES = {0: "RSF_OK", 1: "RSF_PENDING", 2: "RSF_SUSPENDED", -1: "RSF_E_INVAL", -2: "RSF_E_NOMEM", -3: "RSF_E_CUDA",
                 -4: "RSF_E_TIMEOUT", -5: "RSF_E_NOTFOUND", -6: "RSF_E_BUSY", -7: "RSF_E_CANCELLED"}
 RSF_U8, RSF_U16, RSF_F32 = 0, 1, 2
 STAGES = ("f1", "f2", "g", "kappa", "lap")
@@ -27,7 +27,8 @@ STAGES = ("f1", "f2", "g", "kappa", "lap")
 EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_stages", "rsf_prof_enable",
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
-            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0", "rsf_overlap", "rsf_isosurface")
+            "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0", "rsf_overlap", "rsf_isosurface",
+            "rsf_suspend")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
@@ -58,7 +59,7 @@ class ServeStat(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
                 ("cancelled", ctypes.c_uint64), ("queued", ctypes.c_uint64), ("voxel_iterations", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("latency_p50_s", ctypes.c_double), ("latency_p99_s", ctypes.c_double),
-                ("latency_max_s", ctypes.c_double)]
+                ("latency_max_s", ctypes.c_double), ("suspended", ctypes.c_uint64)]
 
 
 class RSFError(RuntimeError):
@@ -117,6 +118,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_wait.restype = i32
     L.rsf_cancel.argtypes = [vp, ctypes.c_uint64]
     L.rsf_cancel.restype = i32
+    L.rsf_suspend.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32)]
+    L.rsf_suspend.restype = i32
     L.rsf_serve_stats.argtypes = [vp, ctypes.POINTER(ServeStat)]
     L.rsf_serve_stats.restype = i32
     L.rsf_set_option.argtypes = [vp, i32, i64]
@@ -357,7 +360,7 @@ class Context:
         return int(t.value)
 
     def poll(self, ticket: int):
-        """(status, latency_s): status RSF_PENDING (1) or RSF_OK (0); errors raise."""
+        """(status, latency_s): status RSF_PENDING (1), RSF_OK (0) or RSF_SUSPENDED (2); errors raise."""
         lat = ctypes.c_double(-1.0)
         try:
             st = _check(load_library().rsf_poll(self._h, int(ticket), ctypes.byref(lat)))
@@ -381,6 +384,15 @@ class Context:
 
     def cancel(self, ticket: int):
         _check(load_library().rsf_cancel(self._h, int(ticket)))
+
+    def suspend(self, ticket: int):
+        """rsf_suspend: returns a ctypes.c_int32 that holds the completed iterations
+        once the ticket resolves with SUSPENDED."""
+        done = ctypes.c_int32(-1)
+        _check(load_library().rsf_suspend(self._h, int(ticket), ctypes.byref(done)))
+        # the library writes it when the ticket resolves: keep it alive until then
+        self._live[int(ticket)] = tuple(self._live.get(int(ticket), ())) + (done,)
+        return done
 
     def serve_stats(self) -> dict:
         st = ServeStat()

@@ -42,11 +42,13 @@ def dev(a):
 
 def footprint(shape, storage_bytes=4):
     """Device bytes of one served brick: phi and q pairs, profiles, constants, and
-    the intermediate fields at an x pitch rounded up to 32 (FP32 storage)."""
+    the intermediate fields at an x pitch rounded up to 32: the x/y-convolved
+    group-A pair (8), (a, b) in the storage type, the x/y-convolved (a, b) (8)
+    and K*I (4) per pitched voxel."""
     nz, ny, nx = shape
     n = nx * ny * nz
     np_ = ((nx + 31) // 32 * 32) * ny * nz
-    return 16 * n + 6 * storage_bytes * np_ + 8 * np_ + 4 * 4096
+    return 16 * n + (8 + 2 * storage_bytes + 8 + 4) * np_ + 4 * 4096
 
 
 @pytest.fixture(scope="module")
