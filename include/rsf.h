@@ -277,6 +277,17 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   path (RSF_E_INVAL otherwise).  rsf_evolve, rsf_step_stages
  *                   and rsf_evolve_batch read it per call; rsf_submit per
  *                   request.
+ *   RSF_OPT_POISON  1: before each solve (rsf_evolve, rsf_step_stages, each
+ *                   brick of rsf_evolve_batch, each served request at
+ *                   admission) fill the working fields the iteration writes
+ *                   before it reads them -- the intermediate fields, the
+ *                   second phi buffer and both Heaviside-argument buffers --
+ *                   with all-ones bytes, a NaN in FP32, FP16 and BF16: a
+ *                   result that depends on memory the iteration did not write
+ *                   then carries NaN or differs from the unpoisoned one (a
+ *                   check for tests, in place of a memory sanitizer); 0
+ *                   (default): off.  Read per call; the serving loop reads it
+ *                   when it starts.
  * The paths give the same result per voxel up to the order of FP32 rounding.
  * Errors: RSF_E_INVAL (unknown key or value).
  */
@@ -288,6 +299,7 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 #define RSF_OPT_FAULT_ADMISSION 6
 #define RSF_OPT_SERVE_SLOTS 7
 #define RSF_OPT_FORCE 8
+#define RSF_OPT_POISON 9
 #define RSF_FORCE_LI 0
 #define RSF_FORCE_EQ15 1
 #define RSF_PATH_AUTO 0

@@ -461,6 +461,10 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
                     c->opt_path);
     // the tiled path reads the image in its own type and centres it on load
     RSF_CUDA(rsf::setup_image(vol, (int)vt, taps, f, c->stream, !tiled));
+    if (c->opt_poison) {  // NaN bytes in everything the iteration must write before it reads
+        RSF_CUDA(cudaMemsetAsync(f.t[0], 0xFF, sizeof(float) * 8 * (size_t)c->cap_np, c->stream));
+        for (float *p : {f.phi[1], f.q[0], f.q[1]}) RSF_CUDA(cudaMemsetAsync(p, 0xFF, sizeof(float) * n, c->stream));
+    }
     RSF_CUDA(xfer(f.phi[0], phi0, sizeof(float) * n, c->stream));
     RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
     int cur = 0;
@@ -583,6 +587,9 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
             return RSF_OK;
         case RSF_OPT_AUTOTUNE:
             c->opt_autotune = value != 0;
+            return RSF_OK;
+        case RSF_OPT_POISON:
+            c->opt_poison = value != 0;
             return RSF_OK;
         case RSF_OPT_GRAPH:
             c->opt_graph = value != 0;

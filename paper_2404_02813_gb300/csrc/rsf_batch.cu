@@ -221,6 +221,10 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         f.cs = cs;
         f.prof = prof;
         RSF_CUDA(rsf::setup_image(d.img, (int)b.vt, make_taps(b.sigma), f, c->stream, false));
+        if (c->opt_poison) {  // NaN bytes in everything the iteration must write before it reads
+            RSF_CUDA(cudaMemsetAsync(d.u2, 0xFF, rsf::tiled_stage_bytes(storage, np), c->stream));
+            for (float *q : {d.phi[1], d.q[0], d.q[1]}) RSF_CUDA(cudaMemsetAsync(q, 0xFF, sizeof(float) * n, c->stream));
+        }
         RSF_CUDA(xfer(d.phi[0], b.phi0, sizeof(float) * n, c->stream));
         if (b.iters > 0) {
             RSF_CUDA(rsf::tiled_q_init(d.phi[0], d.q[0], n, b.eps, c->stream));

@@ -52,6 +52,7 @@ struct rsf_ctx {
     void *server = nullptr;             // the serving loop (rsf_serve.cu), created by rsf_submit
     int64_t opt_inject_admission = 0;   // host-side fault injection for the serving loop
     int64_t opt_serve_slots = 64;       // bricks the serving loop advances together at most
+    int opt_poison = 0;                 // fill working fields with NaN bytes before each solve (tests)
 };
 
 // One launch group before upload: bricks sharing radius, image type, storage.

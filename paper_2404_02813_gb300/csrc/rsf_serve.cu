@@ -111,6 +111,7 @@ struct Server {
     // host-side fault injection: the k-th admission (1-based) fails its set-up
     int64_t inject_admission = 0;
     int64_t slots = 64;  // bricks advanced together at most
+    bool poison = false; // NaN bytes in each brick's working fields at admission (tests)
 };
 
 void CUDART_CB done_cb(void *p) {
@@ -249,6 +250,12 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
         ch.count = (int)std::min<size_t>(kParamChunk, pr.size() - o);
         memcpy(ch.v, pr.data() + o, sizeof(float) * ch.count);
         k_put<<<(ch.count + 255) / 256, 256, 0, s->s_setup>>>(ch, prof);
+    }
+    if (s->poison) {  // NaN bytes in everything the iteration must write before it reads
+        if (cudaMemsetAsync(d.u2, 0xFF, rsf::tiled_stage_bytes(r->storage, np), s->s_setup) != cudaSuccess)
+            return fail_admit(RSF_E_CUDA);
+        for (float *p : {d.phi[1], d.q[0], d.q[1]})
+            if (cudaMemsetAsync(p, 0xFF, sizeof(float) * n, s->s_setup) != cudaSuccess) return fail_admit(RSF_E_CUDA);
     }
     if (xfer(d.phi[0], q.phi0, sizeof(float) * n, s->s_setup) != cudaSuccess)
         return fail_admit(RSF_E_CUDA);
@@ -440,6 +447,7 @@ Server *server(rsf_ctx *c, rsf_status *st) {
     }
     s->inject_admission = c->opt_inject_admission;
     s->slots = c->opt_serve_slots;
+    s->poison = c->opt_poison != 0;
     s->th = std::thread(loop, s);
     c->server = s;
     return s;
