@@ -538,16 +538,20 @@ __device__ __forceinline__ void az_issue(const GroupArgs &G, const AZSlabId &id,
     const int col = threadIdx.x & 31;
     const long long pplane = (long long)B.px * B.ny;
     const long long c0 = (long long)id.y * B.px + id.x0 + col;
-    for (int row = threadIdx.x >> 5; row < ROWS; row += kAZThreads / 32) {
-        const int zi = id.z0 - R + row;
-        const bool ok = (unsigned)zi < (unsigned)B.nz;
-        cp_async8(buf + row * 32 + col, B.u2 + c0 + (long long)(ok ? zi : 0) * pplane, ok);
+    const int nz = B.nz, row0 = threadIdx.x >> 5;
+    constexpr int kStep = kAZThreads / 32;  // rows per pass of the warps
+    // running source offsets, one plane step per row; rows outside the brick copy
+    // nothing (source size 0) from the field's first element
+    long long off_u = c0 + (long long)(id.z0 - R + row0) * pplane;
+    for (int row = row0; row < ROWS; row += kStep, off_u += kStep * pplane) {
+        const bool ok = (unsigned)(id.z0 - R + row) < (unsigned)nz;
+        cp_async8(buf + row * 32 + col, B.u2 + (ok ? off_u : 0), ok);
     }
     float *kb = reinterpret_cast<float *>(buf + ROWS * 32);
-    for (int row = threadIdx.x >> 5; row < kAZT; row += kAZThreads / 32) {
-        const int zi = id.z0 + row;
-        const bool ok = zi < B.nz;
-        cp_async4(kb + row * 32 + col, B.ki + c0 + (long long)(ok ? zi : 0) * pplane, ok);
+    long long off_k = c0 + (long long)(id.z0 + row0) * pplane;
+    for (int row = row0; row < kAZT; row += kStep, off_k += kStep * pplane) {
+        const bool ok = id.z0 + row < nz;
+        cp_async4(kb + row * 32 + col, B.ki + (ok ? off_k : 0), ok);
     }
 }
 
