@@ -864,6 +864,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     float2 ring[M];
 #pragma unroll
     for (int s = 0; s < 2 * R + 2; ++s) ring[s] = load(s);
+    long long aoff = (long long)(z0 + R + 2) * pplane;  // offset of the next step's first (a, b) plane
     float iv0 = active ? centred(img, (long long)z0 * plane, inv_s, nms) : 0.f;
     float iv1 = (active && nout > 1) ? centred(img, (long long)(z0 + 1) * plane, inv_s, nms) : 0.f;
     // p_z of the step's two planes, loaded a step ahead like the image
@@ -877,8 +878,13 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
             if (r0 < nout) {
                 const int zo = z0 + r0;
                 // loads of the next step: (a, b) planes s = 2k + 2R + 2, +3
-                ring[(2 * kk + 2 * R + 2) % M] = load(r0 + 2 * R + 2);
-                ring[(2 * kk + 2 * R + 3) % M] = load(r0 + 2 * R + 3);
+                {  // (a, b) planes s = r0 + 2R + 2, + 3, i.e. z = zo + R + 2, + 3, from a running offset
+                    const bool in2 = active && r0 + 2 < nout && zo + R + 2 < nz;
+                    const bool in3 = active && r0 + 3 < nout && zo + R + 3 < nz;
+                    ring[(2 * kk + 2 * R + 2) % M] = in2 ? __ldg(src + aoff) : make_float2(0.f, 0.f);
+                    ring[(2 * kk + 2 * R + 3) % M] = in3 ? __ldg(src + aoff + pplane) : make_float2(0.f, 0.f);
+                    aoff += 2 * pplane;
+                }
                 store_phi(phi_at(2 * kk + 4), pva);
                 store_phi(phi_at(2 * kk + 5), pvb);
                 fetch_phi(zo + 6, pva);
