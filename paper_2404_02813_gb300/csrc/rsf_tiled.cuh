@@ -865,6 +865,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
 #pragma unroll
     for (int s = 0; s < 2 * R + 2; ++s) ring[s] = load(s);
     long long aoff = (long long)(z0 + R + 2) * pplane;  // offset of the next step's first (a, b) plane
+    long long zoff = (long long)z0 * plane;              // offset of the step's first output plane
     float iv0 = active ? centred(img, (long long)z0 * plane, inv_s, nms) : 0.f;
     float iv1 = (active && nout > 1) ? centred(img, (long long)(z0 + 1) * plane, inv_s, nms) : 0.f;
     // p_z of the step's two planes, loaded a step ahead like the image
@@ -877,8 +878,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
             const int r0 = 2 * k;          // relative output plane
             if (r0 < nout) {
                 const int zo = z0 + r0;
-                // loads of the next step: (a, b) planes s = 2k + 2R + 2, +3
-                {  // (a, b) planes s = r0 + 2R + 2, + 3, i.e. z = zo + R + 2, + 3, from a running offset
+                {  // the next step's (a, b) planes s = r0 + 2R + 2, + 3 (z = zo + R + 2, + 3), running offset
                     const bool in2 = active && r0 + 2 < nout && zo + R + 2 < nz;
                     const bool in3 = active && r0 + 3 < nout && zo + R + 3 < nz;
                     ring[(2 * kk + 2 * R + 2) % M] = in2 ? __ldg(src + aoff) : make_float2(0.f, 0.f);
@@ -890,8 +890,8 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
                 fetch_phi(zo + 6, pva);
                 fetch_phi(zo + 7, pvb);
                 const float im0 = iv0, im1 = iv1, pz0 = kz0, pz1 = kz1;
-                if (active && r0 + 2 < nout) iv0 = centred(img, (long long)(zo + 2) * plane, inv_s, nms);
-                if (active && r0 + 3 < nout) iv1 = centred(img, (long long)(zo + 3) * plane, inv_s, nms);
+                if (active && r0 + 2 < nout) iv0 = centred(img, zoff + 2 * plane, inv_s, nms);
+                if (active && r0 + 3 < nout) iv1 = centred(img, zoff + 3 * plane, inv_s, nms);
                 if (R != 0 && r0 + 2 < nout) kz0 = __ldg(profz + r0 + 2);
                 if (R != 0 && r0 + 3 < nout) kz1 = __ldg(profz + r0 + 3);
                 __syncthreads();
@@ -924,7 +924,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
                                             nrm_at(2 * kk + c - 1)[2 * NH * NW + nc0])) * 0.5f;
                         const float del = eps_pi * rcp_approx(eps2 + ph * ph);  // Eq. (14)
                         const float pn = ph + dt * (mu * (lap - kap) + del * (nu * kap - g));
-                        const long long qz = (long long)(zo + c) * plane;
+                        const long long qz = zoff + c * plane;
                         phi_out[qz] = pn;
                         q_out[qz] = heaviside_q_fast(pn, eps);
                         if (dump) {
@@ -934,6 +934,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
                         }
                     }
                 }
+                zoff += 2 * plane;
             }
         }
     }
