@@ -61,9 +61,9 @@ PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
 NCU_TRAFFIC = {
-    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "69c363a2c15835db",
+    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "f795d4d6476f93ce",
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
-    for k, v in {"rsf_ta_xy": 13.30, "rsf_ta_z": 19.33, "rsf_tb_xy": 15.27, "rsf_tb_z": 21.96}.items()
+    for k, v in {"rsf_ta_xy": 13.29, "rsf_ta_z": 19.34, "rsf_tb_xy": 15.28, "rsf_tb_z": 21.94}.items()
 }
 
 # Issue slots per voxel measured by ncu (smsp__inst_executed.sum * 32 / voxels: warp
@@ -71,9 +71,9 @@ NCU_TRAFFIC = {
 # NCU_TRAFFIC.  The kernels are issue-bound; against one warp instruction per
 # cycle per SM sub-partition (4 per SM) this gives the issue roofline.
 NCU_INST = {
-    k: {"inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "69c363a2c15835db",
+    k: {"inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "f795d4d6476f93ce",
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage"}
-    for k, v in {"rsf_ta_xy": 121.9, "rsf_ta_z": 128.1, "rsf_tb_xy": 96.0, "rsf_tb_z": 253.4}.items()
+    for k, v in {"rsf_ta_xy": 121.9, "rsf_ta_z": 123.1, "rsf_tb_xy": 96.0, "rsf_tb_z": 245.5}.items()
 }
 SM_SUBPARTITIONS = 4  # warp schedulers per SM, one warp instruction issued per cycle each
 

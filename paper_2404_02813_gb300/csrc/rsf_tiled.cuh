@@ -878,20 +878,31 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
             const int r0 = 2 * k;          // relative output plane
             if (r0 < nout) {
                 const int zo = z0 + r0;
-                {  // the next step's (a, b) planes s = r0 + 2R + 2, + 3 (z = zo + R + 2, + 3), running offset
+                // the next step's (a, b) planes s = r0 + 2R + 2, + 3 (z = zo + R + 2, + 3): from a
+                // running offset at radius <= 6 (measured faster there; slower in the 128-register
+                // variants of radius >= 8, which keep the per-plane offsets)
+                if constexpr (R <= 6) {
                     const bool in2 = active && r0 + 2 < nout && zo + R + 2 < nz;
                     const bool in3 = active && r0 + 3 < nout && zo + R + 3 < nz;
                     ring[(2 * kk + 2 * R + 2) % M] = in2 ? __ldg(src + aoff) : make_float2(0.f, 0.f);
                     ring[(2 * kk + 2 * R + 3) % M] = in3 ? __ldg(src + aoff + pplane) : make_float2(0.f, 0.f);
                     aoff += 2 * pplane;
+                } else {
+                    ring[(2 * kk + 2 * R + 2) % M] = load(r0 + 2 * R + 2);
+                    ring[(2 * kk + 2 * R + 3) % M] = load(r0 + 2 * R + 3);
                 }
                 store_phi(phi_at(2 * kk + 4), pva);
                 store_phi(phi_at(2 * kk + 5), pvb);
                 fetch_phi(zo + 6, pva);
                 fetch_phi(zo + 7, pvb);
                 const float im0 = iv0, im1 = iv1, pz0 = kz0, pz1 = kz1;
-                if (active && r0 + 2 < nout) iv0 = centred(img, zoff + 2 * plane, inv_s, nms);
-                if (active && r0 + 3 < nout) iv1 = centred(img, zoff + 3 * plane, inv_s, nms);
+                if constexpr (R <= 6) {
+                    if (active && r0 + 2 < nout) iv0 = centred(img, zoff + 2 * plane, inv_s, nms);
+                    if (active && r0 + 3 < nout) iv1 = centred(img, zoff + 3 * plane, inv_s, nms);
+                } else {
+                    if (active && r0 + 2 < nout) iv0 = centred(img, (long long)(zo + 2) * plane, inv_s, nms);
+                    if (active && r0 + 3 < nout) iv1 = centred(img, (long long)(zo + 3) * plane, inv_s, nms);
+                }
                 if (R != 0 && r0 + 2 < nout) kz0 = __ldg(profz + r0 + 2);
                 if (R != 0 && r0 + 3 < nout) kz1 = __ldg(profz + r0 + 3);
                 __syncthreads();
@@ -924,7 +935,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
                                             nrm_at(2 * kk + c - 1)[2 * NH * NW + nc0])) * 0.5f;
                         const float del = eps_pi * rcp_approx(eps2 + ph * ph);  // Eq. (14)
                         const float pn = ph + dt * (mu * (lap - kap) + del * (nu * kap - g));
-                        const long long qz = zoff + c * plane;
+                        const long long qz = R <= 6 ? zoff + c * plane : (long long)(zo + c) * plane;
                         phi_out[qz] = pn;
                         q_out[qz] = heaviside_q_fast(pn, eps);
                         if (dump) {
