@@ -44,14 +44,10 @@ __device__ __forceinline__ float heaviside_c(float u, float eps) {
     return u < 0.f ? 1.f - r : r;
 }
 
-// The small side of Eq. (10), r = atan(eps/|u|)/pi in (0, 1/2], carrying the
-// sign of u: H = -q for q < 0, else 1 - q; 1 - H = 1 + q for q < 0, else q.
-// These give exactly heaviside() and heaviside_c() of the same u.
-__device__ __forceinline__ float heaviside_q(float u, float eps) {
-    return copysignf(atanf(eps / fabsf(u)) * INV_PI, u);
-}
+// The tiled path stores the small side of Eq. (10), q = atan(eps/|u|)/pi in
+// (0, 1/2], carrying the sign of u (heaviside_q_fast in rsf_tiled.cuh); H is
+// -q for q < 0, else 1 - q.
 __device__ __forceinline__ float h_of_q(float q) { return q < 0.f ? -q : 1.f - q; }
-__device__ __forceinline__ float hc_of_q(float q) { return q < 0.f ? 1.f + q : q; }
 
 // sqrt and reciprocal by the hardware approximations (PTX sqrt.approx.f32,
 // rcp.approx.ftz.f32, relative error of a few ulp); used for the unit normal only.
