@@ -79,3 +79,24 @@ def test_serving_entry_points_validate_without_a_gpu(lib):
     assert lib.rsf_wait(None, 1, 0) == -1
     assert lib.rsf_cancel(None, 1) == -1
     assert lib.rsf_evolve_batch(None, None, 0) == -1
+
+
+def test_new_entry_points_validate_without_a_gpu(lib):
+    import ctypes as C
+    n = C.c_int64()
+    done = C.c_int32()
+    assert lib.rsf_suspend(None, 1, C.byref(done)) == -1
+    assert lib.rsf_isosurface(None, None, 4, 4, 4, C.c_float(0.0), None, None, 0, C.byref(n)) == -1
+    assert lib.rsf_overlap(None, None, None, 0, None) == -1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without librsf.so the binding raises instead of computing anything."""
+    from paper_2404_02813_gb300 import rsf
+    saved = rsf._lib
+    rsf._lib = None
+    try:
+        with pytest.raises(RuntimeError, match="not built"):
+            rsf.load_library(str(tmp_path / "librsf.so"))
+    finally:
+        rsf._lib = saved
