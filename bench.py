@@ -37,15 +37,16 @@ sys.path.insert(0, ROOT)
 # image's byte size (the tiled kernels read it in its own type), `st` the
 # storage byte size of (a, b) (4, or 2 for FP16/BF16).
 def algo_bytes_per_voxel(img: int, st: int, force: str = "li") -> dict:
-    # the Eq. (15) form writes (a, b) in FP32 from rsf_ta_z and has no rsf_tb_xy
-    ab_out = 8 if force == "eq15" else 2 * st
+    eq15 = force == "eq15"
+    # the Eq. (15) form: rsf_ta_xy writes both sides of Eq. (10) (two FP32 pairs), rsf_ta_z reads them
+    # and writes the FP32 fits (f1, f2), no K*I~, no rsf_tb_xy
     return {
         # six-pass schedule (FP32 fields, centred FP32 image)
         "rsf_a_x": 4 + 4 + 16, "rsf_a_y": 16 + 16, "rsf_a_z": 16 + 8,
         "rsf_b_x": 8 + 8, "rsf_b_y": 8 + 8, "rsf_b_z": 8 + 4 + 4 + 4,
         # tiled schedule
-        "rsf_ta_xy": 4 + img + 8,               # q, I -> x/y-convolved (H I~, H), FP32
-        "rsf_ta_z": 8 + 4 + ab_out,             # (H I~, H), K*I~ -> (a, b)
+        "rsf_ta_xy": 4 + img + (16 if eq15 else 8),     # q, I -> x/y-convolved pair(s), FP32
+        "rsf_ta_z": 16 + 8 if eq15 else 8 + 4 + 2 * st,  # pair(s) (, K*I~) -> (f1, f2) / (a, b)
         "rsf_tb_xy": 2 * st + 8,                # (a, b) -> x/y-convolved (a, b), FP32
         "rsf_tb_z": 8 + img + 4 + 4 + 4,        # (a, b)_xy, I, phi -> phi', q(phi')
     }

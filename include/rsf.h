@@ -49,7 +49,7 @@ typedef int32_t rsf_status;
 #define RSF_E_INVAL (-1)     /* bad argument: null pointer, dim < 4, NaN or non-positive sigma/eps/dt, iters < 0 */
 #define RSF_E_NOMEM (-2)     /* the HBM budget or a device allocation was exceeded */
 #define RSF_E_CUDA (-3)      /* a CUDA runtime call failed; see rsf_last_error() */
-#define RSF_E_TIMEOUT (-4)   /* a bounded wait expired */
+#define RSF_E_TIMEOUT (-4)   /* rsf_wait: its time limit expired before a final status */
 #define RSF_E_NOTFOUND (-5)  /* unknown ticket */
 #define RSF_E_BUSY (-6)      /* queue full */
 #define RSF_E_CANCELLED (-7) /* request cancelled */
@@ -267,6 +267,13 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   k-th admission with RSF_E_CUDA, on the host, without any
  *                   device work (for testing failure handling); 0: off.  Read
  *                   when the serving loop starts (the first rsf_submit).
+ *   RSF_OPT_FAULT_UPLOAD  k > 0: the serving loop's k-th upload of the active
+ *                   bricks' launch descriptors fails on the host, without any
+ *                   device work (for testing failure handling); the requests
+ *                   active at that tick resolve RSF_E_CUDA with phi_out
+ *                   unwritten, queued ones are served afterwards; 0: off.
+ *                   (A failed launch of a tick is handled the same way.)  Read
+ *                   when the serving loop starts (the first rsf_submit).
  *   RSF_OPT_FORCE   the data terms e_1, e_2 of the force: RSF_FORCE_LI
  *                   (default), Li et al.'s e_i = (K*1) I^2 - 2 I K*f_i +
  *                   K*(f_i^2), read into Eqs. (11)-(12), which convolve the
@@ -300,6 +307,7 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 #define RSF_OPT_SERVE_SLOTS 7
 #define RSF_OPT_FORCE 8
 #define RSF_OPT_POISON 9
+#define RSF_OPT_FAULT_UPLOAD 10
 #define RSF_FORCE_LI 0
 #define RSF_FORCE_EQ15 1
 #define RSF_PATH_AUTO 0

@@ -236,8 +236,6 @@ rsf_status ensure_fields(rsf_ctx *c, int nx, int ny, int nz) {
         if (st) return st;
         st = dev_alloc(c, (void **)&c->f.partials, sizeof(float) * 3 * rsf::kStatBlocks);
         if (st) return st;
-        st = dev_alloc(c, (void **)&c->f.err, sizeof(int));
-        if (st) return st;
     }
     c->f.d = d;
     c->f.px = px;
@@ -404,7 +402,6 @@ extern "C" void rsf_destroy(rsf_ctx *c) {
         free_fields(c);
         dev_free(c, c->f.cs, sizeof(float) * 4);
         dev_free(c, c->f.partials, sizeof(float) * 3 * rsf::kStatBlocks);
-        dev_free(c, c->f.err, sizeof(int));
         dev_free(c, c->staging, c->staging_cap);
         dev_free(c, c->dump, c->dump_cap);
         free_desc(c, c->desc);
@@ -426,7 +423,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     if (st) return st;
     rsf::Fields &f = c->f;
     const long long n = f.d.n;
-    bool ready = f.I && f.prof && f.cs && f.partials && f.err && f.phi[0] && f.phi[1] && f.q[0] && f.q[1];
+    bool ready = f.I && f.prof && f.cs && f.partials && f.phi[0] && f.phi[1] && f.q[0] && f.q[1];
     for (float *p : f.t) ready = ready && p;
     if (!ready) return fail(RSF_E_CUDA, "internal error: working fields are not allocated");
     float *dump = nullptr;
@@ -466,7 +463,6 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         for (float *p : {f.phi[1], f.q[0], f.q[1]}) RSF_CUDA(cudaMemsetAsync(p, 0xFF, sizeof(float) * n, c->stream));
     }
     RSF_CUDA(xfer(f.phi[0], phi0, sizeof(float) * n, c->stream));
-    RSF_CUDA(cudaMemsetAsync(f.err, 0, sizeof(int), c->stream));
     int cur = 0;
     if (tiled) {
         RSF_CUDA(rsf::tiled_prepare(storage, taps.R, force));
@@ -482,7 +478,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         b.phi[1] = f.phi[1];
         b.q[0] = f.q[0];
         b.q[1] = f.q[1];
-        rsf::tiled_stage_views(storage, f.t[0], (long long)f.px * ny * nz, &b.u2, &b.ab, &b.abxy, &b.ki);
+        rsf::tiled_stage_views(storage, force, f.t[0], (long long)f.px * ny * nz, &b.u2, &b.ab, &b.abxy, &b.ki);
         b.eps = eps;
         b.lambda1 = lambda1;
         b.lambda2 = lambda2;
@@ -527,12 +523,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     RSF_CUDA(xfer(phi_out, f.phi[cur], sizeof(float) * n, c->stream));
     if (stages && dump != stages)
         RSF_CUDA(xfer(stages, dump, sizeof(float) * n * RSF_NSTAGES, c->stream));
-    int err_word = 0;
-    RSF_CUDA(cudaMemcpyAsync(&err_word, f.err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     RSF_CUDA(cudaStreamSynchronize(c->stream));
-    if (err_word == rsf::kErrTimeout)
-        return fail(RSF_E_TIMEOUT, "a bounded wait in a pipelined kernel expired; phi_out is not valid");
-    if (err_word != 0) return fail(RSF_E_CUDA, "kernel error word %d", err_word);
     return RSF_OK;
 }
 
@@ -584,6 +575,10 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
         case RSF_OPT_FAULT_ADMISSION:
             if (value < 0) return fail(RSF_E_INVAL, "fault admission index must be >= 0");
             c->opt_inject_admission = value;
+            return RSF_OK;
+        case RSF_OPT_FAULT_UPLOAD:
+            if (value < 0) return fail(RSF_E_INVAL, "fault upload index must be >= 0");
+            c->opt_inject_upload = value;
             return RSF_OK;
         case RSF_OPT_AUTOTUNE:
             c->opt_autotune = value != 0;

@@ -200,7 +200,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         d.prof = prof;
         d.cs = cs;
         const long long np = (long long)px * b.ny * b.nz;
-        rsf::tiled_stage_views(storage, take(rsf::tiled_stage_bytes(storage, np)), np, &d.u2, &d.ab, &d.abxy, &d.ki);
+        rsf::tiled_stage_views(storage, force, take(rsf::tiled_stage_bytes(storage, np)), np, &d.u2, &d.ab, &d.abxy, &d.ki);
         if (stage_img[i]) {
             void *img = take(dtype_size(b.vt) * n);
             RSF_CUDA(xfer(img, b.volume, dtype_size(b.vt) * n, c->stream));

@@ -50,7 +50,8 @@ struct rsf_ctx {
     std::mutex alloc_mu;                // guards `used` (the serving thread allocates too)
     std::mutex serve_mu;                // guards creation of the serving loop
     void *server = nullptr;             // the serving loop (rsf_serve.cu), created by rsf_submit
-    int64_t opt_inject_admission = 0;   // host-side fault injection for the serving loop
+    int64_t opt_inject_admission = 0;   // host-side fault injection for the serving loop: an admission
+    int64_t opt_inject_upload = 0;      // and a descriptor upload of the active set
     int64_t opt_serve_slots = 64;       // bricks the serving loop advances together at most
     int opt_poison = 0;                 // fill working fields with NaN bytes before each solve (tests)
 };

@@ -48,6 +48,8 @@ __device__ __forceinline__ float heaviside_c(float u, float eps) {
 // (0, 1/2], carrying the sign of u (heaviside_q_fast in rsf_tiled.cuh); H is
 // -q for q < 0, else 1 - q.
 __device__ __forceinline__ float h_of_q(float q) { return q < 0.f ? -q : 1.f - q; }
+// 1 - H for the same q: 1 + q for q < 0, else q (its small side is q itself).
+__device__ __forceinline__ float hc_of_q(float q) { return q < 0.f ? 1.f + q : q; }
 
 // sqrt and reciprocal by the hardware approximations (PTX sqrt.approx.f32,
 // rcp.approx.ftz.f32, relative error of a few ulp); used for the unit normal only.

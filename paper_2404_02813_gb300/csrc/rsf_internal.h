@@ -66,11 +66,9 @@ struct Fields {
                               // capacity >= px * ny * nz (the tiled path's pitched fields use the block
                               // as u (float4), ab and abxy (float2) at offsets 0, 4 np, 6 np)
     int px = 0;               // x pitch of the tiled path's intermediate fields (multiple of 32)
-    int *err = nullptr;       // device error word written by bounded waits (0 = none)
 };
 
 constexpr int kStatBlocks = 1024;
-constexpr int kErrTimeout = 1;  // value of Fields::err after an expired bounded wait
 
 // Set-up: centring constants, the K*1 profiles and (when `centre`) the
 // centred image f.I.  `vol` is a device pointer of dtype vt (0 u8, 1 u16, 2 f32).
@@ -97,9 +95,11 @@ struct BrickDev {
     const float *cs;        // centring constants [m, 1/s, s^2, s]
     const float *prof;      // K*1 profiles p_x[nx], p_y[ny], p_z[nz]
     float *phi[2], *q[2];   // ping-pong level set and its q = +-atan(eps/|phi|)/pi
-    float2 *u2;             // pitched x/y-convolved (H I~, H), FP32
+    float2 *u2;             // pitched x/y-convolved (H I~, H), FP32 (Eq. (15) form: one float4 per voxel,
+                            // ((H I~, H), ((1-H) I~, 1-H)))
     void *ab;               // pitched (a, b), storage type
-    float2 *abxy;           // pitched x/y-convolved (a, b), FP32 (also the set-up's scratch for ki)
+    float2 *abxy;           // pitched x/y-convolved (a, b), FP32 (also the set-up's scratch for ki;
+                            // Eq. (15) form: the fits (f1, f2))
     float *ki;              // pitched K*I~ (the centred image convolved), FP32, set once per solve
     float eps, lambda1, lambda2, nu, mu, dt;
     int zc;                 // z chunk of the update kernel
@@ -126,10 +126,15 @@ cudaError_t tiled_prepare(int storage, int R, int force);
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
 void tiled_cta_counts(const BrickDev &b, unsigned counts[4]);
 size_t tiled_stage_bytes(int storage, long long np);
-void tiled_stage_views(int storage, void *base, long long np, float2 **u2, void **ab, float2 **abxy, float **ki);
+// Views of one brick's intermediate fields in a block of tiled_stage_bytes(storage, np)
+// bytes, for Li's form (force 0) or the Eq. (15) form (u2 then holds two pairs per
+// voxel, abxy the fits (f1, f2); ab and ki are null).
+void tiled_stage_views(int storage, int force, void *base, long long np, float2 **u2, void **ab, float2 **abxy,
+                       float **ki);
 // q = +-atan(eps/|phi|)/pi (sign of phi) before the first tiled iteration.
 cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s);
-// b.ki = K*I~ before the first tiled iteration (b.img, b.cs set; uses b.abxy as scratch).
+// b.ki = K*I~ before the first tiled iteration (b.img, b.cs set; uses b.abxy as scratch);
+// nothing when b.ki is null (the Eq. (15) form).
 cudaError_t tiled_ki_init(const BrickDev &b, int imgtype, const Taps &taps, cudaStream_t s);
 
 // One iteration of the separable pass path: phi_in -> phi_out.

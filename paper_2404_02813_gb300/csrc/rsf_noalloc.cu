@@ -23,6 +23,7 @@
 #include <mutex>
 
 #include "rsf.h"
+#include "rsf_ctx.h"
 #include "rsf_internal.h"
 
 namespace {
@@ -75,13 +76,16 @@ rsf_status scratch_on_current_device(float **out) {
     return RSF_OK;
 }
 
-bool is_device_ptr(const void *p) {
+// Memory the kernels of device `dev` may read and write in place: device memory
+// of that device, or managed memory.  (Device memory of another GPU is refused:
+// without peer access a kernel here would fault on it.)
+bool is_device_ptr(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return (a.type == cudaMemoryTypeDevice && a.device == dev) || a.type == cudaMemoryTypeManaged;
 }
 
 // Values written into the static array through kernel parameters, so that no
@@ -117,8 +121,11 @@ extern "C" rsf_status rsf_evolve_noalloc(const void *volume, rsf_dtype vt, int64
     if (!(eps > 0.f) || !std::isfinite(eps)) return err(RSF_E_INVAL, "eps must be positive and finite");
     if (!(dt > 0.f) || !std::isfinite(dt)) return err(RSF_E_INVAL, "dt must be positive and finite");
     if (iters < 0) return err(RSF_E_INVAL, "iters must be >= 0");
-    if (!is_device_ptr(volume) || !is_device_ptr(phi0) || !is_device_ptr(phi_out))
-        return err(RSF_E_INVAL, "rsf_evolve_noalloc takes device pointers only");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return err(RSF_E_CUDA, cudaGetErrorString(e));
+    if (!is_device_ptr(volume, dev) || !is_device_ptr(phi0, dev) || !is_device_ptr(phi_out, dev))
+        return err(RSF_E_INVAL, "rsf_evolve_noalloc takes device pointers of the current device only");
 
     float *base = nullptr;
     rsf_status st = scratch_on_current_device(&base);
@@ -135,35 +142,20 @@ extern "C" rsf_status rsf_evolve_noalloc(const void *volume, rsf_dtype vt, int64
     float *scratch_phi = base + kOffPhi;
     const long long n = f.d.n;
 
-    rsf::Taps taps{};
-    taps.R = R;
-    double w[2 * rsf::RMAX + 1], sum = 0.0;
-    for (int k = -R; k <= R; ++k) {
-        w[k + R] = std::exp(-(double)k * k / (2.0 * (double)sigma * (double)sigma));
-        sum += w[k + R];
-    }
-    for (int k = 0; k < 2 * R + 1; ++k) taps.g[k] = (float)(w[k] / sum);
+    const rsf::Taps taps = make_taps(sigma);
     const rsf::Coeffs co{eps, lambda1, lambda2, nu, mu, dt};
 
-    cudaError_t e;
     if (iters == 0) {
         if (phi_out != phi0) e = cudaMemcpyAsync(phi_out, phi0, sizeof(float) * n, cudaMemcpyDeviceToDevice, s);
         else e = cudaSuccess;
         return e == cudaSuccess ? RSF_OK : err(RSF_E_CUDA, cudaGetErrorString(e));
     }
     if ((e = rsf::centre_image(volume, (int)vt, f, s)) != cudaSuccess) return err(RSF_E_CUDA, cudaGetErrorString(e));
-    // zero-padding profiles p_a(i) = sum_{k: 0 <= i+k < n_a} g[k] (K*1 = p_x p_y p_z), summed
-    // on the host in double exactly as rsf_evolve does, so both give the same K*1
+    // zero-padding profiles (K*1 = p_x p_y p_z), by the same host routine as rsf_evolve's;
+    // nx + ny + nz <= kMaxProfile within the voxel limit
     float prof[kMaxProfile];
-    const int n3[3] = {(int)nx, (int)ny, (int)nz};
-    int np = 0;
-    for (int a = 0; a < 3; ++a)
-        for (int i = 0; i < n3[a]; ++i) {
-            double acc = 0.0;
-            for (int k = -R; k <= R; ++k)
-                if (i + k >= 0 && i + k < n3[a]) acc += (double)taps.g[k + R];
-            prof[np++] = (float)acc;
-        }
+    const int np = (int)(nx + ny + nz);
+    rsf::zero_padding_profiles(taps, (int)nx, (int)ny, (int)nz, prof);
     for (int o = 0; o < np; o += kParamChunk) {
         ParamChunk c;
         c.offset = o;

@@ -108,8 +108,11 @@ struct Server {
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, suspended = 0, admitted = 0;
     double vox_iters = 0.0, t_first = 0.0, t_last = 0.0;
     std::vector<double> latencies;
-    // host-side fault injection: the k-th admission (1-based) fails its set-up
+    // host-side fault injection: the k-th admission (1-based) fails its set-up;
+    // the k-th descriptor upload of the active set fails
     int64_t inject_admission = 0;
+    int64_t inject_upload = 0;
+    uint64_t uploads = 0;
     int64_t slots = 64;  // bricks advanced together at most
     bool poison = false; // NaN bytes in each brick's working fields at admission (tests)
 };
@@ -219,7 +222,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     d.prof = prof;
     d.cs = cs;
     const long long np = (long long)px * q.ny * q.nz;
-    rsf::tiled_stage_views(r->storage, take(rsf::tiled_stage_bytes(r->storage, np)), np, &d.u2, &d.ab, &d.abxy, &d.ki);
+    rsf::tiled_stage_views(r->storage, r->force, take(rsf::tiled_stage_bytes(r->storage, np)), np, &d.u2, &d.ab, &d.abxy, &d.ki);
     if (stage_img) {
         void *img = take(dtype_size(q.vt) * n);
         if (xfer(img, q.volume, dtype_size(q.vt) * n, s->s_setup) != cudaSuccess)
@@ -270,17 +273,17 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     return true;
 }
 
-// Retire an active request after its last launch: copy out (unless cancelled;
-// a suspended request copies phi after its done_iters iterations, the buffer of
-// that parity), stamp completion, return its memory in stream order.
-void retire(Server *s, const std::shared_ptr<Request> &r, bool cancelled, bool suspended = false) {
+// Retire an active request after its last launch with `outcome`: RSF_OK and
+// RSF_SUSPENDED copy phi after its done_iters iterations (the buffer of that
+// parity) to the caller; RSF_E_CANCELLED and RSF_E_CUDA (a launch or upload of
+// its tick failed) copy nothing.  Stamps completion, returns its memory in
+// stream order.
+void retire(Server *s, const std::shared_ptr<Request> &r, int outcome) {
     rsf_ctx *c = s->ctx;
-    int st = suspended ? RSF_SUSPENDED : RSF_OK;
-    if (cancelled) {
-        st = RSF_E_CANCELLED;
-    } else if (xfer(r->req.phi_out, r->d.phi[r->done_iters & 1], sizeof(float) * r->n, s->s_comp) != cudaSuccess) {
+    int st = outcome;
+    if ((st == RSF_OK || st == RSF_SUSPENDED) &&
+        xfer(r->req.phi_out, r->d.phi[r->done_iters & 1], sizeof(float) * r->n, s->s_comp) != cudaSuccess)
         st = RSF_E_CUDA;
-    }
     cudaLaunchHostFunc(s->s_comp, done_cb, new DoneArg{s, r, st});
     cudaFreeAsync(r->mem, s->s_comp);
     if (r->ready) cudaEventDestroy(r->ready);
@@ -289,7 +292,9 @@ void retire(Server *s, const std::shared_ptr<Request> &r, bool cancelled, bool s
     c->used -= std::min<uint64_t>(c->used, r->bytes);
 }
 
-void rebuild_groups(Server *s) {
+// Launch groups of the active set; false (and the groups left empty) when the
+// descriptor upload failed.
+bool rebuild_groups(Server *s) {
     std::vector<std::shared_ptr<Request>> order = s->active;
     std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a->n > b->n; });
     std::vector<GroupSpec> specs;
@@ -320,8 +325,19 @@ void rebuild_groups(Server *s) {
     // the copy comes from pageable memory and waits for the compute stream; the
     // loop already bounds how far it runs ahead, so this costs one short sync
     s->groups.clear();
-    upload_groups(s->ctx, s->desc, s->s_comp, specs, &s->groups);
+    rsf_status st;
+    if (s->inject_upload > 0 && (int64_t)++s->uploads == s->inject_upload) {
+        rsf::set_last_error("injected descriptor upload failure");
+        st = RSF_E_CUDA;
+    } else {
+        st = upload_groups(s->ctx, s->desc, s->s_comp, specs, &s->groups);
+    }
+    if (st != RSF_OK) {
+        s->groups.clear();
+        return false;
+    }
     s->groups_dirty = false;
+    return true;
 }
 
 void loop(Server *s) {
@@ -373,7 +389,7 @@ void loop(Server *s) {
                 cudaStreamWaitEvent(s->s_comp, r->ready, 0);
                 r->done_iters = 0;
                 if (r->req.iters == 0) {
-                    retire(s, r, false);
+                    retire(s, r, RSF_OK);
                 } else {
                     s->active.push_back(r);
                     s->groups_dirty = true;
@@ -381,8 +397,19 @@ void loop(Server *s) {
             }
         }
         if (s->active.empty()) continue;
-        if (s->groups_dirty) rebuild_groups(s);
-        for (const rsf::TiledGroup &g : s->groups) rsf::tiled_iterate(g, (int)(s->tick & 1), nullptr, s->s_comp);
+        // a tick counts only if the upload and every launch of it succeeded; otherwise the
+        // requests of the active set fail with RSF_E_CUDA (queued ones are admitted later)
+        bool ok = !s->groups_dirty || rebuild_groups(s);
+        for (const rsf::TiledGroup &g : s->groups)
+            if (ok && rsf::tiled_iterate(g, (int)(s->tick & 1), nullptr, s->s_comp) != cudaSuccess) ok = false;
+        if (!ok) {
+            cudaGetLastError();  // not sticky: later launches are not blamed for it
+            for (auto &r : s->active) retire(s, r, RSF_E_CUDA);
+            s->active.clear();
+            s->groups.clear();
+            s->groups_dirty = true;
+            continue;
+        }
         ++s->tick;
         // retire finished or cancelled bricks
         std::vector<std::shared_ptr<Request>> keep;
@@ -393,7 +420,7 @@ void loop(Server *s) {
             const bool finished = r->done_iters >= r->req.iters;
             const bool suspended = !cancelled && !finished && r->suspend.load();
             if (cancelled || finished || suspended) {
-                retire(s, r, cancelled, suspended);
+                retire(s, r, cancelled ? RSF_E_CANCELLED : (suspended ? RSF_SUSPENDED : RSF_OK));
                 s->groups_dirty = true;
             } else {
                 keep.push_back(r);
@@ -420,7 +447,7 @@ void loop(Server *s) {
         s->queue.clear();
     }
     for (auto &r : rest) finish_now(s, r, RSF_E_CANCELLED);
-    for (auto &r : s->active) retire(s, r, true);
+    for (auto &r : s->active) retire(s, r, RSF_E_CANCELLED);
     s->active.clear();
     cudaStreamSynchronize(s->s_comp);
     cudaStreamSynchronize(s->s_setup);
@@ -446,6 +473,7 @@ Server *server(rsf_ctx *c, rsf_status *st) {
         return nullptr;
     }
     s->inject_admission = c->opt_inject_admission;
+    s->inject_upload = c->opt_inject_upload;
     s->slots = c->opt_serve_slots;
     s->poison = c->opt_poison != 0;
     s->th = std::thread(loop, s);

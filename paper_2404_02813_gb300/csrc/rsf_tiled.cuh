@@ -39,6 +39,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "rsf_internal.h"
 
@@ -139,8 +140,6 @@ struct GroupArgs {
     const int *starts;  // nb + 1 CTA offsets of this kernel within the launch
     int nb;
     int parity;         // launch parity: a brick reads phi[p], q[p] with p = parity ^ flip, writes the other
-    int ab_f32;         // 1: rsf_ta_z writes (a, b) in FP32 to abxy, where the update kernel of the
-                        // Eq. (15) form reads them without group-B convolutions
 };
 
 // ---------------------------------------------------------------- x / y
@@ -163,6 +162,16 @@ struct ProH {  // (H I~, H) from q and the centred image
     __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
         const float h = h_of_q(r.q);
         v[0] = inside ? make_float2(h * r.im, h) : make_float2(0.f, 0.f);
+    }
+};
+
+template <class ImgT>
+struct ProH2 : ProH<ImgT> {  // (H I~, H) and ((1-H) I~, 1-H): both sides of Eq. (10) for the Eq. (15) form
+    using typename ProH<ImgT>::Raw;
+    __device__ __forceinline__ void apply(const Raw &r, bool inside, float2 *v) const {
+        const float h = h_of_q(r.q), hc = hc_of_q(r.q);
+        v[0] = inside ? make_float2(h * r.im, h) : make_float2(0.f, 0.f);
+        v[1] = inside ? make_float2(hc * r.im, hc) : make_float2(0.f, 0.f);
     }
 };
 
@@ -270,9 +279,9 @@ template <> struct Vec4<uint8_t> { using V = uchar4; };
 template <> struct Vec4<uint16_t> { using V = ushort4; };
 template <> struct Vec4<float> { using V = float4; };
 
-template <int R, class ImgT>
-struct VecLoaderH {
-    using L = XYLayout<R, 1>;
+template <int R, class ImgT, int NP = 1>
+struct VecLoaderH {  // NP = 1: (H I~, H); NP = 2: also ((1-H) I~, 1-H) (the Eq. (15) form)
+    using L = XYLayout<R, NP>;
     static_assert(R % 2 == 0 && R <= 8, "even radius <= 8");
     static constexpr int RA = (R + 3) / 4 * 4;
     static constexpr int NG = (32 + 2 * RA) / 4;                       // groups per row
@@ -317,23 +326,26 @@ struct VecLoaderH {
             }
         }
     }
-    __device__ __forceinline__ float2 pair(float qv, float iv, bool inside) const {
-        const float h = h_of_q(qv);
-        return inside ? make_float2(h * fmaf(iv, inv_s, nms), h) : make_float2(0.f, 0.f);
+    // two adjacent columns (q, image value) of each input pair into the tile at index c
+    __device__ __forceinline__ void put(float2 *in, int c, float qa, float ia, float qb, float ib, bool inside) const {
+        const float ha = h_of_q(qa), hb = h_of_q(qb);
+        const float xa = fmaf(ia, inv_s, nms), xb = fmaf(ib, inv_s, nms);
+        *reinterpret_cast<float4 *>(in + c) =
+            inside ? make_float4(ha * xa, ha, hb * xb, hb) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (NP == 2) {
+            const float ca = hc_of_q(qa), cb = hc_of_q(qb);
+            *reinterpret_cast<float4 *>(in + L::H * L::P + c) =
+                inside ? make_float4(ca * xa, ca, cb * xb, cb) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     }
     __device__ __forceinline__ void store(float2 *in) const {
 #pragma unroll
         for (int e = 0; e < NV; ++e) {
             const int c0 = sm0[e], lx = lx0[e];
             const bool inside = goff[e] >= 0;
-            if (lx >= 0 && lx + 1 < L::W) {
-                const float2 a = pair(rq[e].x, (float)ri[e].x, inside), b = pair(rq[e].y, (float)ri[e].y, inside);
-                *reinterpret_cast<float4 *>(in + c0) = make_float4(a.x, a.y, b.x, b.y);
-            }
-            if (lx != kNone && lx + 2 >= 0 && lx + 3 < L::W) {
-                const float2 a = pair(rq[e].z, (float)ri[e].z, inside), b = pair(rq[e].w, (float)ri[e].w, inside);
-                *reinterpret_cast<float4 *>(in + c0 + 2) = make_float4(a.x, a.y, b.x, b.y);
-            }
+            if (lx >= 0 && lx + 1 < L::W) put(in, c0, rq[e].x, (float)ri[e].x, rq[e].y, (float)ri[e].y, inside);
+            if (lx != kNone && lx + 2 >= 0 && lx + 3 < L::W)
+                put(in, c0 + 2, rq[e].z, (float)ri[e].z, rq[e].w, (float)ri[e].w, inside);
         }
     }
 };
@@ -428,6 +440,16 @@ struct OutF2 {  // one x/y-convolved pair, FP32, pitched
     __device__ __forceinline__ void operator()(float2 *pl, int o, float2 a, float2) const { pl[o] = a; }
 };
 
+struct OutF4 {  // two x/y-convolved pairs interleaved per voxel (16 bytes), FP32, pitched
+    float4 *u;
+    int px;
+    long long pplane;
+    __device__ __forceinline__ float4 *plane(int z) const { return u + (long long)z * pplane; }
+    __device__ __forceinline__ void operator()(float4 *pl, int o, float2 a, float2 b) const {
+        pl[o] = make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+
 // CTA -> (brick, tile) for the x/y kernels: tiles (tx, ty, tz) of 32 x 32 x kXYPlanes.
 struct XYTile {
     int b, x0, y0, za;
@@ -439,8 +461,12 @@ __device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev 
     return XYTile{b, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes};
 }
 
-template <int R, class ImgT>
-__global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 3) k_ta_xy(GroupArgs G, TapPairs t) {
+// NP = 1: (H I~, H) into B.u2 (Li's form); NP = 2: both sides of Eq. (10),
+// ((H I~, H), ((1-H) I~, 1-H)) interleaved per voxel into B.u2 read as float4
+// (the Eq. (15) form, which convolves the complement directly).
+template <int R, class ImgT, int NP = 1>
+__global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <= 8 ? 3 : 2))
+    k_ta_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
     const BrickDev B = G.bricks[b];
@@ -448,20 +474,27 @@ __global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 3) k_ta_xy(GroupArgs 
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
     const float *q = (G.parity ^ B.flip) ? B.q[1] : B.q[0];
     const ImgT *img = reinterpret_cast<const ImgT *>(B.img);
-    OutF2 out{B.u2, B.px, (long long)B.px * B.ny};
+    using Out = typename std::conditional<NP == 1, OutF2, OutF4>::type;
+    using OutV = typename std::conditional<NP == 1, float2, float4>::type;
+    const Out out{reinterpret_cast<OutV *>(B.u2), B.px, (long long)B.px * B.ny};
     if constexpr (R % 2 == 0 && R <= 6) {
         // four columns per load where the row pitch and both base addresses allow it (uniform per CTA);
         // at radius 8 the second code path cost more registers than the loads saved (measured)
         if (B.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(img) % (4 * sizeof(ImgT)) == 0) {
-            VecLoaderH<R, ImgT> ld(q, img, inv_s, nms, B.nx, B.ny, tl.x0, tl.y0);
-            xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
+            VecLoaderH<R, ImgT, NP> ld(q, img, inv_s, nms, B.nx, B.ny, tl.x0, tl.y0);
+            xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
             return;
         }
     }
-    ProH<ImgT> pro{q, img, inv_s, nms};
-    ScalarLoader<R, 1, ProH<ImgT>> ld(pro, B.nx, B.ny, B.nx, tl.x0, tl.y0);
-    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
+    using Pro = typename std::conditional<NP == 1, ProH<ImgT>, ProH2<ImgT>>::type;
+    Pro pro{};
+    pro.q = q;
+    pro.img = img;
+    pro.inv_s = inv_s;
+    pro.nms = nms;
+    ScalarLoader<R, NP, Pro> ld(pro, B.nx, B.ny, B.nx, tl.x0, tl.y0);
+    xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
 }
 
 template <int R, class S>
@@ -497,6 +530,10 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -593,9 +630,9 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
             const long long pplane = (long long)B.px * B.ny;
             const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
             V2 *ab = reinterpret_cast<V2 *>(B.ab) + off;
-            float2 *abf = B.abxy + off;
             const float *ki = reinterpret_cast<const float *>(buf + ROWS * 32) + zb * 32 + lane;
             const float kxy = __ldg(B.prof + x) * __ldg(B.prof + B.nx + id.y);
+            float2 res = make_float2(0.f, 0.f);  // rounding residual carried along z (16-bit storage)
             const float *pz = B.prof + B.nx + B.ny + id.z0 + zb;
             float *const dump = B.dump;
 #pragma unroll
@@ -612,10 +649,116 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
                     const float k1 = kxy * __ldg(pz + o), den = k1 - acc.y;
                     const float f2 = den > 0x1p-20f * k1 ? __fdividef(ki[o * 32] - acc.x, den) : f1;
                     const float2 v = make_float2(l1 * f1 - l2 * f2, l1 * (f1 * f1) - l2 * (f2 * f2));
-                    if (G.ab_f32)
-                        abf[o * pplane] = v;
-                    else
-                        ab[o * pplane] = Store<S>::pack2(v);
+                    if constexpr (std::is_same<S, float>::value) {
+                        ab[o * pplane] = v;
+                    } else {
+                        // 16-bit storage: the rounding residual of each plane is carried into the
+                        // next plane of the column before it is rounded (first-order noise
+                        // shaping along z), so that the stored field's rounding error is a
+                        // difference of neighbours, which the Gaussian of group B averages out
+                        const float2 want = make_float2(v.x + res.x, v.y + res.y);
+                        const V2 st = Store<S>::pack2(want);
+                        const float2 got = Store<S>::unpack2(st);
+                        res = make_float2(want.x - got.x, want.y - got.y);
+                        ab[o * pplane] = st;
+                    }
+                    if (dump) {
+                        const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
+                        const long long n = (long long)B.nx * B.ny * B.nz;
+                        dump[q] = f1 * B.cs[3] + B.cs[0];
+                        dump[n + q] = f2 * B.cs[3] + B.cs[0];
+                    }
+                }
+            }
+        }
+        __syncthreads();  // this stage is refilled by the next iteration's copies
+        stage ^= 1;
+    }
+}
+
+// The z pass of the Eq. (15) form: the same x-z slabs and persistent walk,
+// over the four x/y-convolved fields ((H I~, H), ((1-H) I~, 1-H)) staged as
+// one float4 per row and column; writes the fits f1 = K*(H I~)/K*H and
+// f2 = K*((1-H) I~)/K*(1-H) (Eq. 6, both sides convolved directly) in FP32
+// to B.abxy, where the update kernel forms (I~ - f_i)^2 (Eq. 15, sigma_2 = 0).
+template <int R>
+constexpr int az4_stage() { return (kAZT + 2 * R) * 32; }  // float4 units per stage
+template <int R>
+constexpr size_t az4_smem() { return 2 * sizeof(float4) * az4_stage<R>(); }
+
+template <int R>
+__device__ __forceinline__ void az4_issue(const GroupArgs &G, const AZSlabId &id, float4 *buf) {
+    constexpr int ROWS = kAZT + 2 * R;
+    constexpr int kStep = kAZThreads / 32;  // rows per pass of the warps
+    const BrickDev &B = G.bricks[id.b];
+    const int col = threadIdx.x & 31;
+    const long long pplane = (long long)B.px * B.ny;
+    const long long c0 = (long long)id.y * B.px + id.x0 + col;
+    const int nz = B.nz, row0 = threadIdx.x >> 5;
+    const float4 *u4 = reinterpret_cast<const float4 *>(B.u2);
+    long long off = c0 + (long long)(id.z0 - R + row0) * pplane;
+    for (int row = row0; row < ROWS; row += kStep, off += kStep * pplane) {
+        const bool ok = (unsigned)(id.z0 - R + row) < (unsigned)nz;
+        cp_async16(buf + row * 32 + col, u4 + (ok ? off : 0), ok);
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(kAZThreads, 2) k_ta_z4(GroupArgs G, TapPairs t) {
+    constexpr int T = 2 * R + 1;
+    constexpr int WIN = kAZO + 2 * R;
+    constexpr int STAGE = az4_stage<R>();
+    extern __shared__ float4 slab4[];  // [2 stages][ROWS][32]
+    const int total = __ldg(G.starts + G.nb);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int stage = 0;
+    AZSlabId next{};
+    if ((int)blockIdx.x < total) {
+        next = az_slab_of(G, blockIdx.x);
+        az4_issue<R>(G, next, slab4);
+    }
+    cp_async_commit();
+    for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
+        const AZSlabId id = next;
+        if (sl + (int)gridDim.x < total) {
+            next = az_slab_of(G, sl + gridDim.x);
+            az4_issue<R>(G, next, slab4 + (stage ^ 1) * STAGE);
+        }
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const float4 *buf = slab4 + stage * STAGE;
+        const BrickDev &B = G.bricks[id.b];
+        const int x = id.x0 + lane;
+        const int zb = warp * kAZO;
+        if (x < B.nx) {
+            // the two pairs one after the other, each over a window of float2 entries
+            // (one float4 window of 8 + 2R entries spills at radius >= 10)
+            float2 acc[2][kAZO];  // (K*(H I~), K*H), (K*((1-H) I~), K*(1-H))
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const float2 *b2 = reinterpret_cast<const float2 *>(buf) + p;
+                float2 w[WIN];
+#pragma unroll
+                for (int j = 0; j < WIN; ++j) w[j] = b2[2 * ((zb + j) * 32 + lane)];
+#pragma unroll
+                for (int o = 0; o < kAZO; ++o) {
+                    float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int k = 0; k < T; ++k) a = f2fma(t.g[k], w[o + k], a);
+                    acc[p][o] = a;
+                }
+            }
+            const long long pplane = (long long)B.px * B.ny;
+            const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
+            float2 *fits = B.abxy + off;
+            float *const dump = B.dump;
+#pragma unroll
+            for (int o = 0; o < kAZO; ++o) {
+                const int zo = id.z0 + zb + o;
+                if (zo < B.nz) {
+                    const float f1 = __fdividef(acc[0][o].x, acc[0][o].y), f2 = __fdividef(acc[1][o].x, acc[1][o].y);
+                    fits[o * pplane] = make_float2(f1, f2);
                     if (dump) {
                         const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
                         const long long n = (long long)B.nx * B.ny * B.nz;
@@ -844,7 +987,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     // take no convolution and K*1 is 1
     const float pxy = R == 0 ? 1.f : (active ? __ldg(B.prof + x) * __ldg(B.prof + nx + y) : 0.f);
     const float *profz = B.prof + nx + ny + z0;
-    const float l12 = B.lambda1 - B.lambda2, s2 = B.cs[2];
+    const float l1 = B.lambda1, l2 = B.lambda2, l12 = l1 - l2, s2 = B.cs[2];
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
     const float eps = B.eps, eps_pi = eps * INV_PI, eps2 = eps * eps;
     const float mu = B.mu, nu = B.nu, dt = B.dt;
@@ -921,8 +1064,14 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
 #pragma unroll
                         for (int kt = 0; kt < T; ++kt) acc = f2fma(t.g[kt], ring[(2 * kk + c + kt) % M], acc);
                         const float im = c ? im1 : im0;
-                        const float K1 = R == 0 ? 1.f : pxy * (c ? pz1 : pz0);
-                        const float g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
+                        float g;
+                        if constexpr (R == 0) {  // Eq. (15), sigma_2 = 0: the ring holds (f1, f2)
+                            const float d1 = im - acc.x, d2 = im - acc.y;
+                            g = s2 * (l1 * (d1 * d1) - l2 * (d2 * d2));
+                        } else {  // Li's data terms from K*a, K*b
+                            const float K1 = pxy * (c ? pz1 : pz0);
+                            g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
+                        }
                         const float *p0 = phi_at(2 * kk + c);
                         const int pc0 = (ty + 2) * PW + tx + 2;
                         const float ph = p0[pc0];
@@ -987,9 +1136,10 @@ cudaError_t prepare_storage() {
                                 (int)XYLayout<R, 1>::bytes);
 }
 
+// One iteration of Li's form (group A, group B, update) for radius R and storage S.
 template <int R, class S>
 cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, nullptr, g.nb, parity, g.force};
+    GroupArgs G{g.bricks, nullptr, g.nb, parity};
     const TapPairs tp = tap_pairs(g.taps);
     {
         ProfScope ps(prof, KID_TA_XY);
@@ -1007,7 +1157,7 @@ cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cuda
         const unsigned grid = g.ncta[1] < (unsigned)az_persist<R, S>() ? g.ncta[1] : (unsigned)az_persist<R, S>();
         k_ta_z<R, S><<<grid, kAZThreads, az_smem<R>(), s>>>(G, tp);
     }
-    if (!g.force) {  // the Eq. (15) form has no group-B convolutions
+    {
         ProfScope ps(prof, KID_TB_XY);
         G.starts = g.starts[2];
         constexpr size_t sm = XYLayout<R, 1>::bytes;

@@ -9,7 +9,7 @@ namespace tiled {
 namespace {
 template <int R, class ImgT>
 cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, g.starts[3], g.nb, parity, 0};
+    GroupArgs G{g.bricks, g.starts[3], g.nb, parity};
     ProfScope ps(prof, KID_TB_Z);
     Taps t = g.taps;
     if (R == 0) {  // the Eq. (15) form: one unit tap, no convolution of (a, b)
@@ -93,9 +93,13 @@ cudaError_t tiled_launch_bf16(const TiledGroup &g, int parity, Profiler *prof, c
 cudaError_t tiled_prepare_f16(int R);
 cudaError_t tiled_prepare_bf16(int R);
 
+cudaError_t tiled_prepare_eq15(int R);
+cudaError_t tiled_launch_eq15(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
+
 cudaError_t tiled_prepare(int storage, int R, int force) {
     const cudaError_t e = tiled::prepare_tb_z(force ? 0 : R);
     if (e != cudaSuccess) return e;
+    if (force) return tiled_prepare_eq15(R);  // FP32 intermediates whatever the storage option
     switch (storage) {
         case 0: return tiled::prepare_group_s<float>(R);
         case 1: return tiled_prepare_bf16(R);
@@ -105,6 +109,7 @@ cudaError_t tiled_prepare(int storage, int R, int force) {
 }
 
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
+    if (g.force) return tiled_launch_eq15(g, parity, prof, s);
     switch (g.storage) {
         case 0: return tiled::launch_group_s<float>(g, parity, prof, s);
         case 1: return tiled_launch_bf16(g, parity, prof, s);
@@ -123,17 +128,27 @@ void tiled_cta_counts(const BrickDev &b, unsigned counts[4]) {
                 ((b.nz + b.zc - 1) / b.zc);
 }
 
-// Per pitched voxel: (H I~, H) 8 bytes, (a, b) 2 elements of the storage type,
-// x/y-convolved (a, b) 8 bytes, K*I~ 4 bytes (np is even: every view is 8-byte aligned).
+// Per pitched voxel, Li's form: (H I~, H) 8 bytes, (a, b) 2 elements of the
+// storage type, x/y-convolved (a, b) 8 bytes, K*I~ 4 bytes (24 or 28 bytes; np
+// is even: every view is 8-byte aligned).  The Eq. (15) form: the two
+// x/y-convolved pairs 16 bytes, the fits (f1, f2) 8 bytes (24 bytes, within
+// the count for every storage type; no (a, b), no K*I~).
 size_t tiled_stage_bytes(int storage, long long np) {
     const size_t e = storage == 0 ? 4 : 2;
     return (8 + 2 * e + 8 + 4) * (size_t)np;
 }
 
-void tiled_stage_views(int storage, void *base, long long np, float2 **u2, void **ab, float2 **abxy, float **ki) {
-    const size_t e = storage == 0 ? 4 : 2;
+void tiled_stage_views(int storage, int force, void *base, long long np, float2 **u2, void **ab, float2 **abxy,
+                       float **ki) {
     char *p = static_cast<char *>(base);
     *u2 = reinterpret_cast<float2 *>(p);
+    if (force) {
+        *ab = nullptr;
+        *abxy = reinterpret_cast<float2 *>(p + 16 * np);
+        *ki = nullptr;
+        return;
+    }
+    const size_t e = storage == 0 ? 4 : 2;
     *ab = p + 8 * np;
     *abxy = reinterpret_cast<float2 *>(p + (8 + 2 * e) * np);
     *ki = reinterpret_cast<float *>(p + (16 + 2 * e) * np);
@@ -161,6 +176,7 @@ cudaError_t ki_init_i(const BrickDev &b, int imgtype, const Taps &taps, cudaStre
 }  // namespace
 
 cudaError_t tiled_ki_init(const BrickDev &b, int imgtype, const Taps &taps, cudaStream_t s) {
+    if (!b.ki) return cudaSuccess;  // the Eq. (15) form convolves the complement directly
     switch (taps.R) {
         case 2: return ki_init_i<2>(b, imgtype, taps, s);
         case 3: return ki_init_i<3>(b, imgtype, taps, s);

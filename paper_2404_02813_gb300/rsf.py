@@ -33,6 +33,7 @@ EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_s
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
 OPT_POISON = 9
+OPT_FAULT_UPLOAD = 10
 PATHS = {"auto": 0, "passes": 1, "tiled": 2}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 # data-term forms: Li et al.'s (default) and the paper's Eq. (15) with sigma_2 = 0

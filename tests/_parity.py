@@ -33,32 +33,6 @@ def storage_force_tol(phi_n, dump, params, unit_roundoff, factor=4.0):
     return factor * unit_roundoff * params["dt"] * delta * mag
 
 
-def fits_force_tol(vol, phi_n, dump, params, factor=8.0):
-    """Allowance for the FP32 rounding of the background fit f2 under the Eq. (15)
-    form (e_i = (I - f_i)^2 enters g unaveraged).
-
-    The GPU forms f2 = K*((1-H) I) / K*(1-H) from the convolution's linearity
-    as (K*I - K*(H I)) / (K*1 - K*H), with I centred on the image mean m.  Each
-    convolved field carries a few FP32 roundoffs u of the sum of the magnitudes
-    it adds up, so the absolute error of f2 is about
-    factor * u * (K*|I - m| + |f2 - m| K*1) / K*(1-H);
-    through e2 = (I - f2)^2 it moves g = l1 e1 - l2 e2 by 2 l2 |I - f2| times that,
-    and phi by dt delta(phi_n) times the change of g.
-    """
-    import oracle
-    I = np.asarray(vol, dtype=np.float64)
-    phi_n = np.asarray(phi_n, dtype=np.float64)
-    eps, sigma = params["eps"], params["sigma"]
-    m = I.mean()
-    k_abs = oracle.conv3(np.abs(I - m), sigma)
-    k_one = oracle.conv3(np.ones_like(I), sigma)
-    k_out = oracle.conv3(1.0 - oracle.heaviside(phi_n, eps), sigma)
-    f2 = dump["f2"]
-    df2 = factor * 2.0 ** -24 * (k_abs + np.abs(f2 - m) * k_one) / k_out
-    delta = (eps / np.pi) / (eps * eps + phi_n * phi_n)
-    return params["dt"] * delta * 2.0 * params["lambda2"] * np.abs(I - f2) * df2
-
-
 def assert_phi_close(out, ref, phi_n, rel=1e-3, what="", force=None, sign_max=1e-4):
     out = np.asarray(out, dtype=np.float64)
     err = np.abs(out - ref)

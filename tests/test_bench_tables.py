@@ -33,7 +33,7 @@ def test_hash_ignores_comments_and_blank_space(tmp_path, monkeypatch):
     assert _hash_of(tmp_path, monkeypatch, "int f(int a) { return a+1; }") != base  # code text, not semantics
 
 
-@pytest.mark.parametrize("img,st,force,total", [(2, 4, "li", 72), (1, 4, "eq15", 54), (1, 2, "li", 62)])
+@pytest.mark.parametrize("img,st,force,total", [(2, 4, "li", 72), (1, 4, "eq15", 66), (1, 2, "li", 62)])
 def test_schedule_bytes(img, st, force, total):
     per = bench.algo_bytes_per_voxel(img, st, force)
     kernels = ["rsf_ta_xy", "rsf_ta_z", "rsf_tb_z"] + ([] if force == "eq15" else ["rsf_tb_xy"])

@@ -124,10 +124,10 @@ def test_bad_arguments(ctx, edge, curtain):
 
 
 def test_curtain_eq15_f16_matches_oracle():
-    """The context's force form and storage apply inside the curtain scheme."""
+    """The context's force form applies inside the curtain scheme (16-bit storage
+    leaves the Eq. (15) form's FP32 intermediates as they are)."""
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
-    from _parity import storage_force_tol
     vol, phi0 = _case((36, 40, 44))
     p = dict(synth.RSFParams().as_dict(), sigma=2.0)
     c = rsf.Context(0)
@@ -137,10 +137,5 @@ def test_curtain_eq15_f16_matches_oracle():
         out = c.evolve_curtain(dev(vol), dev(phi0), p, 1, 24, 4).cpu().numpy()
     finally:
         c.close()
-    # one iteration: the oracle's curtain step, with the stage terms of the whole volume for the
-    # storage allowance (each sub-volume's terms differ from them only near its faces, where the
-    # merge weights fade)
     ref = oracle.curtain_evolve(vol.astype(np.float64), phi0.astype(np.float64), p, 1, 24, 4, force="eq15")
-    _, dump = oracle.step(vol.astype(np.float64), phi0.astype(np.float64), p, dump=True, force="eq15")
-    force = storage_force_tol(phi0, dump, p, 2.0 ** -11)
-    assert_phi_close(out, ref, phi0, rel=2e-2, force=force, sign_max=3e-4, what="curtain eq15 f16")
+    assert_phi_close(out, ref, phi0, rel=1e-3, sign_max=1e-4, what="curtain eq15")

@@ -1,16 +1,15 @@
 """16-bit storage of the intermediate fields (FP16, BF16) against the FP64 oracle.
 
-(a, b) are stored in 16 bits with FP32 accumulation; phi, the image, the
-x/y-convolved group-A pair, K*I and the x/y-convolved (a, b) stay exact / FP32.  The gate is
-the per-iteration bound for reduced storage: 2e-2 * c0, plus eight FP32 ulps of
-|phi|, plus four unit roundoffs of the storage format (2^-11 for FP16) times the
-non-cancelled size of the force, dt * delta(phi_n) * (l1 |e1| + l2 |e2|): the
-rounding of the stored fits enters the data terms relative to their own size,
-and on 16-bit images those terms are ~(P/255)^2 larger than on 8-bit ones.
-BF16 (8-bit significand, unit roundoff 2^-8) does not meet the 2e-2 * c0 part
-on these workloads, nor the 0.01 % sign-disagreement bound (it reaches ~1.3e-4
-on the first step of the 64^3 workload); it is checked against 0.25 * c0 and
-5e-4, the figures recorded for it.
+(a, b) are stored in 16 bits with FP32 accumulation, the rounding residual of
+each plane carried into the next plane of its column (noise shaping along z);
+phi, the image, the x/y-convolved group-A pair, K*I and the x/y-convolved
+(a, b) stay exact / FP32.  The gate, for both formats, is the per-iteration
+bound for reduced storage: 2e-2 * c0, plus eight FP32 ulps of |phi|, plus four
+unit roundoffs of the storage format (2^-11 for FP16, 2^-8 for BF16) times
+the non-cancelled size of the force, dt * delta(phi_n) * (l1 |e1| + l2 |e2|):
+the rounding of the stored fits enters the data terms relative to their own
+size, and on 16-bit images those terms are ~(P/255)^2 larger than on 8-bit
+ones.  Sign disagreement <= 1e-4.
 """
 import numpy as np
 import pytest
@@ -25,9 +24,9 @@ pytestmark = pytest.mark.gpu
 
 from _parity import storage_force_tol
 
-REL = {"f16": 2e-2, "bf16": 0.25}
+REL = {"f16": 2e-2, "bf16": 2e-2}
 UNIT = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}
-SIGN = {"f16": 1e-4, "bf16": 5e-4}
+SIGN = {"f16": 1e-4, "bf16": 1e-4}
 
 
 @pytest.fixture(scope="module", params=["f16", "bf16"])

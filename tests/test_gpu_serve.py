@@ -5,7 +5,8 @@ while others run; each result must equal rsf_evolve on the same brick with the
 same storage, bit for bit (continuous batching changes when a brick's
 iterations run, not how).  Failure handling is exercised on the host only:
 cancellation, a request larger than the HBM budget, admission that waits for
-memory, and an injected set-up failure of one admission.
+memory, an injected set-up failure of one admission, and an injected failure
+of one descriptor upload of the active set.
 """
 import time
 
@@ -159,4 +160,27 @@ def test_injected_admission_failure(cases):
     np.testing.assert_array_equal(outs[2].cpu().numpy(), ref)
     st = ctx.serve_stats()
     assert st["failed"] == 1 and st["completed"] == 2
+    ctx.close()
+
+
+def test_injected_upload_failure(cases):
+    """The first upload of the active set's launch descriptors fails on the host:
+    the requests active at that tick resolve RSF_E_CUDA, with their phi_out left
+    as it was; requests submitted afterwards are served normally."""
+    ctx = rsf.Context(0)
+    ctx.set_option(rsf.OPT_FAULT_UPLOAD, 1)
+    vol, phi0, p, _, _ = cases[6]
+    ref = rsf.Context(0).evolve(dev(vol), dev(phi0), p, 3).cpu().numpy()
+    v, ph = dev(vol), dev(phi0)
+    first = torch.full_like(ph, 7.0)
+    t = ctx.submit(v, ph, p, 3, first)
+    with pytest.raises(rsf.RSFError) as e:
+        ctx.wait(t, 60000)
+    assert e.value.status == -3
+    assert bool((first == 7.0).all())
+    later = torch.empty_like(ph)
+    assert ctx.wait(ctx.submit(v, ph, p, 3, later), 60000) == 0
+    np.testing.assert_array_equal(later.cpu().numpy(), ref)
+    st = ctx.serve_stats()
+    assert st["failed"] == 1 and st["completed"] == 1
     ctx.close()

@@ -78,3 +78,17 @@ def test_noalloc_rejects_volumes_above_its_limit():
         rsf.evolve_noalloc(v.cpu()[:8, :8, :8].contiguous(), ph.cpu()[:8, :8, :8].contiguous(),
                            synth.RSFParams().as_dict(), 1, ph.cpu()[:8, :8, :8].contiguous())
     assert e.value.status == -1
+
+
+def test_noalloc_rejects_memory_of_another_device():
+    """Device memory of a GPU other than the current one is refused before any
+    launch (without peer access a kernel would fault on it)."""
+    if not torch.cuda.is_available() or torch.cuda.device_count() < 2:
+        pytest.skip("needs two GPUs")
+    shape = (8, 8, 8)
+    v = torch.zeros(shape, dtype=torch.uint8, device="cuda:1")
+    ph = torch.zeros(shape, dtype=torch.float32, device="cuda:1")
+    with torch.cuda.device(0):
+        with pytest.raises(rsf.RSFError) as e:
+            rsf.evolve_noalloc(v, ph, synth.RSFParams().as_dict(), 1, ph, stream=torch.cuda.current_stream(0))
+    assert e.value.status == -1
