@@ -587,12 +587,16 @@ def main():
     ap.add_argument("--rates", default="16,32,50,100,200,400", help="Poisson arrival rates in requests/s (serve)")
     ap.add_argument("--bricks", type=int, default=None, help="number of bricks of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lean", action="store_true",
+                    help="the timed step only: no CPU baselines, end-to-end repeat or untimed extras (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="cube edge instead of the workload's (profiling runs)")
     ap.add_argument("--iters", type=int, default=None, help="iterations per step instead of the workload's")
     ap.add_argument("--path", default="auto", choices=["auto", "passes", "tiled"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
+    if args.lean:
+        args.no_cpu_baseline = args.no_e2e = True
     if args.warmup < 3 and args.impl == "rsf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
 
@@ -705,7 +709,7 @@ def main():
     # the segmentation scored against the generator's ground truth (Dice, Jaccard; reported, not timed)
     seg = None
     seg_seeded = None
-    if args.workload in TRUTH:
+    if args.workload in TRUTH and not args.lean:
         truth = torch.from_numpy(TRUTH[args.workload]).cuda()
         seg = ctx.overlap(out, truth)
         seg["note"] = ("phi > 0 after the step's iterations against the voxels of occupancy >= 1/2 before the blur; "

@@ -447,9 +447,10 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     const rsf::Taps taps = make_taps(sigma);
     const rsf::Coeffs co{eps, lambda1, lambda2, nu, mu, dt};
     const int storage = c->opt_storage;
-    const bool tiled = c->opt_path != RSF_PATH_PASSES && rsf::tiled_supports(taps.R);
+    const bool tiled = c->opt_path != RSF_PATH_PASSES && rsf::tiled_supports(taps.R) && rsf::tiled_fits(nx, ny, nz);
     if (c->opt_path == RSF_PATH_TILED && !tiled)
-        return fail(RSF_E_INVAL, "the tiled path has no kernels for radius %d", taps.R);
+        return fail(RSF_E_INVAL, "the tiled path has no kernels for radius %d or for %lld voxels (pitched, 2^32 at most)",
+                    taps.R, (long long)rsf::tiled_pitch((int)nx) * ny * nz);
     if (storage != RSF_STORE_F32 && !tiled)
         return fail(RSF_E_INVAL, "16-bit storage needs the tiled path (radius %d, path option %d)", taps.R, c->opt_path);
     const int force = c->opt_force;

@@ -141,6 +141,8 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         if (st) return fail(st, "brick %d: %s", i, rsf_last_error());
         if (!rsf::tiled_supports(make_taps(b.sigma).R))
             return fail(RSF_E_INVAL, "brick %d: no batched kernels for radius %d", i, make_taps(b.sigma).R);
+        if (!rsf::tiled_fits(b.nx, b.ny, b.nz))
+            return fail(RSF_E_INVAL, "brick %d: 2^32 pitched voxels or more", i);
     }
     std::lock_guard<std::mutex> lk(c->mu);
     RSF_CUDA(cudaSetDevice(c->device));

@@ -121,6 +121,9 @@ struct TiledGroup {
 
 // Tiled four-kernel path (rsf_tiled*.cu) for the radii it is instantiated for.
 bool tiled_supports(int R);
+// The tiled kernels address a brick's pitched fields with 32-bit offsets: they take
+// bricks of fewer than 2^32 pitched voxels.
+bool tiled_fits(long long nx, long long ny, long long nz);
 int tiled_pitch(int nx);
 cudaError_t tiled_prepare(int storage, int R, int force);
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);

@@ -510,6 +510,7 @@ extern "C" rsf_status rsf_submit(rsf_ctx *c, const rsf_request *req, uint64_t *t
         return fail(RSF_E_INVAL, "unknown storage %d", (int)req->storage);
     const int R = make_taps(req->sigma).R;
     if (!rsf::tiled_supports(R)) return fail(RSF_E_INVAL, "no served kernels for radius %d", R);
+    if (!rsf::tiled_fits(req->nx, req->ny, req->nz)) return fail(RSF_E_INVAL, "a brick of 2^32 pitched voxels or more");
     if (req->halo >= 0 && (2 * (int64_t)req->halo >= req->nx || 2 * (int64_t)req->halo >= req->ny ||
                            2 * (int64_t)req->halo >= req->nz))
         return fail(RSF_E_INVAL, "halo %d leaves no core in a %lld x %lld x %lld brick", (int)req->halo,

@@ -824,65 +824,107 @@ __global__ void __launch_bounds__(kAZThreads) k_ki_z(BrickDev B, TapPairs t) {
 // and for |u| < eps, atan(eps/|u|) = pi/2 - atan(|u|/eps).  atan(x)/pi on
 // [0, 1] is x P(x^2), P the degree-8 minimax polynomial of relative error
 // (coefficients by Lawson's algorithm, atan_poly.py), 1.5e-7 relative in FP32.
+// P's coefficients, highest power first (Horner order).
+__device__ constexpr float kAtanPi[9] = {9.071480017e-04f, -5.114803091e-03f, 1.358913258e-02f, -2.388691157e-02f,
+                              3.387114406e-02f, -4.521160573e-02f, 6.363848597e-02f, -1.061024666e-01f,
+                              3.183098733e-01f};
 __device__ __forceinline__ float atan01_pi(float x) {
     const float t = x * x;
-    float p = 9.071480017e-04f;
-    p = fmaf(p, t, -5.114803091e-03f);
-    p = fmaf(p, t, 1.358913258e-02f);
-    p = fmaf(p, t, -2.388691157e-02f);
-    p = fmaf(p, t, 3.387114406e-02f);
-    p = fmaf(p, t, -4.521160573e-02f);
-    p = fmaf(p, t, 6.363848597e-02f);
-    p = fmaf(p, t, -1.061024666e-01f);
-    p = fmaf(p, t, 3.183098733e-01f);
+    float p = kAtanPi[0];
+#pragma unroll
+    for (int k = 1; k < 9; ++k) p = fmaf(p, t, kAtanPi[k]);
     return x * p;
 }
 __device__ __forceinline__ float heaviside_q_fast(float u, float eps) {
     const float a = fabsf(u);
-    const float at = atan01_pi(__fdividef(fminf(a, eps), fmaxf(a, eps)));
+    const float at = atan01_pi(fminf(a, eps) * rcp_approx(fmaxf(a, eps)));
     return copysignf(a >= eps ? at : 0.5f - at, u);
+}
+
+// Packed f32x2 arithmetic (IEEE round-to-nearest per lane) for two planes at once.
+__device__ __forceinline__ float2 f2v(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// heaviside_q_fast of two values with packed arithmetic: per lane the same
+// operations in the same order (the ratio, the polynomial, 1/2 - at), so each
+// lane equals the scalar function bit for bit.
+__device__ __forceinline__ float2 heaviside_q_fast2(float2 u, float eps) {
+    const float ax = fabsf(u.x), ay = fabsf(u.y);
+    const float2 x = f2mul(make_float2(fminf(ax, eps), fminf(ay, eps)),
+                           make_float2(rcp_approx(fmaxf(ax, eps)), rcp_approx(fmaxf(ay, eps))));
+    const float2 t = f2mul(x, x);
+    float2 p = f2v(kAtanPi[0]);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) p = __ffma2_rn(p, t, f2v(kAtanPi[k]));
+    const float2 at = f2mul(x, p);
+    const float2 lo = f2sub(f2v(0.5f), at);
+    return make_float2(copysignf(ax >= eps ? at.x : lo.x, u.x), copysignf(ay >= eps ? at.y : lo.y, u.y));
 }
 
 // z march over a 32x8 column tile of one brick, z chunk [z0, z0 + zc), two
 // output planes per step.  Planes are numbered relative to the chunk start
 // (r = z - z0); ring slots are r mod ring size, so with the step loop unrolled
-// over M planes every slot index is a compile-time constant.
+// over 2 SPB planes every slot index is a compile-time constant.
 //
-// Step k, outputs zo = z0 + 2k and zo + 1:
-//   issue the (a, b) loads of the next step into the register ring; store phi
-//   planes zo+4, zo+5 (fetched one step earlier) into the phi ring and fetch
-//   zo+6, zo+7; barrier; normals of planes zo+3, zo+4; outputs zo, zo+1, which
-//   read phi zo-1 .. zo+2 and the normals of zo-1 .. zo+2 (earlier steps).
-// Ring sizes: phi 16 planes (one step reads zo-3 .. zo+5 across the barrier
-// while the next writes zo+6, zo+7), normals 8 (zo-1 .. zo+4 live), (a, b)
-// M = 16 or 32 register slots (2R+2 planes in use plus 2 in flight).
-// Finite differences use the logical planes, which hold reflect-101 copies
-// outside the brick; the unit normal is itself padded by reflect-101, so the
-// normal of plane -1 is that of plane 1 and the normal of plane nz that of
-// plane nz-2 (the prologue and the step loop copy them).
+// Step k, outputs zo = z0 + 2k and zo + 1: bring in the planes later steps
+// need (below); barrier; unit normals of planes zo+3, zo+4; outputs zo, zo+1,
+// which read phi zo-1 .. zo+2 and the normals of zo-1 .. zo+2 (earlier steps).
+// Rings: phi 16 planes, normals 8, (a, b) in registers M = 16 or 32 (2R+2
+// planes in use plus those of the next step).  Finite differences use the
+// logical planes, which hold reflect-101 copies outside the brick; the unit
+// normal is itself padded by reflect-101, so the normal of plane -1 is that of
+// plane 1 and the normal of plane nz that of plane nz-2 (the prologue and the
+// step loop copy them).
+//
+// Two schedules by radius (measured per radius):
+//   R <= 6: three CTAs per SM at 80 registers.  Step k loads the (a, b) planes
+//     of the next step (zo+R+2, zo+R+3) into the register ring, stores phi
+//     planes zo+4, zo+5 (loaded one step earlier) into the phi ring and loads
+//     zo+6, zo+7, and loads the image and p_z of planes zo+2, zo+3.
+//   R >= 8 (a 32-plane register ring): two CTAs per SM at up to 128
+//     registers, so the loads run two steps ahead to cover the HBM latency at
+//     16 warps per SM.  Step k copies (cp.async) phi planes zo+8, zo+9 straight
+//     into the phi ring and this thread's (a, b) of planes zo+R+6, zo+R+7 into
+//     an 8-plane staging ring, waits for the copies of two steps ago, moves
+//     (a, b) planes zo+R+2, zo+R+3 from the staging ring into the register
+//     ring, and loads the image and p_z of planes zo+4, zo+5.  Offsets within a
+//     field are 32-bit (bricks of fewer than 2^32 pitched voxels).
+template <int R>
+constexpr bool tbz_deep() { return R > 6; }
 template <int R>
 constexpr int tbz_ring() { return 2 * R + 4 <= 4 ? 4 : (2 * R + 4 <= 8 ? 8 : (2 * R + 4 <= 16 ? 16 : 32)); }
 
-constexpr int kZPhiRing = 16, kZNrmRing = 8;
+constexpr int kZPhiRing = 16, kZNrmRing = 8, kZAbRing = 8;
 constexpr int kZPW = kZX + 4, kZPH = kZY + 4;  // phi tile, halo 2
 constexpr int kZNW = kZX + 2, kZNH = kZY + 2;  // normal tile, halo 1
+template <int R>
 constexpr size_t tbz_smem() {
-    return sizeof(float) * (kZPhiRing * kZPH * kZPW + kZNrmRing * 3 * kZNH * kZNW);
+    return sizeof(float) * (kZPhiRing * kZPH * kZPW + kZNrmRing * 3 * kZNH * kZNW) +
+           (tbz_deep<R>() ? sizeof(float2) * kZAbRing * kZThreads : 0);
 }
 
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 template <int R, class ImgT>
-__global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G, TapPairs t) {
+__global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(GroupArgs G, TapPairs t) {
+    constexpr bool DEEP = tbz_deep<R>();
+    using Off = typename std::conditional<DEEP, unsigned, long long>::type;  // offsets within a field
+    constexpr int NIV = DEEP ? 4 : 2;  // image and p_z registers: planes zo .. zo + NIV - 1
     constexpr int T = 2 * R + 1;
     constexpr int M = tbz_ring<R>();
     constexpr int SPB = (M < kZPhiRing ? kZPhiRing : M) / 2;  // steps per unrolled body: 2 SPB planes, a multiple
-                                                              // of the phi, normal and (a, b) ring sizes
+                                                              // of every ring size and of NIV
     constexpr int PW = kZPW, PH = kZPH, NW = kZNW, NH = kZNH;
     constexpr int PPL = PH * PW, NPL = 3 * NH * NW;
     constexpr int NPE = (PH * PW + kZThreads - 1) / kZThreads;
     constexpr int NNE = (NH * NW + kZThreads - 1) / kZThreads;
     extern __shared__ float zsm[];
-    float *const sphi = zsm;                         // [kZPhiRing][PH * PW]
-    float *const snrm = zsm + kZPhiRing * PPL;       // [kZNrmRing][3][NH * NW]
+    float *const sphi = zsm;                                                 // [kZPhiRing][PH * PW]
+    float *const snrm = zsm + kZPhiRing * PPL;                               // [kZNrmRing][3][NH * NW]
+    float2 *const sab = reinterpret_cast<float2 *>(snrm + kZNrmRing * NPL);  // DEEP: [kZAbRing][kZThreads]
 
     const int bi = find_brick(G.starts, G.nb, blockIdx.x);
     const BrickDev B = G.bricks[bi];
@@ -890,7 +932,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     const int nbx = (B.nx + kZX - 1) / kZX, nby = (B.ny + kZY - 1) / kZY;
     const int bx = local % nbx, rr = local / nbx;
     const int nx = B.nx, ny = B.ny, nz = B.nz;
-    const long long plane = (long long)nx * ny;
+    const Off plane = (Off)nx * (Off)ny;
 
     const int tx = threadIdx.x & (kZX - 1), ty = threadIdx.x / kZX;
     const int x0 = bx * kZX, y0 = (rr % nby) * kZY;
@@ -901,8 +943,12 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     const int nout = z1 - z0;
     const int nplanes = nout + 2 * R;  // (a, b) planes of the chunk, r = -R .. nout + R - 1
     const long long col = (long long)min(y, ny - 1) * nx + min(x, nx - 1);
+    // this thread's column: in its pointers (R <= 6) or in its 32-bit offsets, from warp-uniform
+    // field bases (R >= 8)
+    const long long colp = DEEP ? 0 : col;
+    const Off colo = DEEP ? (Off)col : (Off)0;
     const int px = B.px;
-    const long long pplane = (long long)px * ny;
+    const Off pplane = (Off)px * (Off)ny;
     const int par = G.parity ^ B.flip;
     const float *phi = par ? B.phi[1] : B.phi[0];
 
@@ -923,9 +969,14 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
         const int qy = refl101(clampi(y0 + ly - 1, -1, ny), ny);
         noff[e] = clampi(qy - y0 + 2, 1, PH - 2) * PW + clampi(qx - x0 + 2, 1, PW - 2);
     }
-    // phi plane z (logical, -2 .. nz+1 hold reflect-101 copies) into registers / the ring
+    auto phi_at = [&](int r) { return sphi + ((r + kZPhiRing) & (kZPhiRing - 1)) * PPL; };
+    auto nrm_at = [&](int r) { return snrm + ((r + kZNrmRing) & (kZNrmRing - 1)) * NPL; };
+    auto ab_at = [&](int s) { return sab + (s & (kZAbRing - 1)) * kZThreads; };
+    // phi plane z (logical, -2 .. nz+1 hold reflect-101 copies; planes past nz+1, never read, are
+    // clamped): into registers and then the ring (R <= 6), or copied into the ring (R >= 8)
+    auto phi_plane = [&](int z) { return phi + (Off)refl101(clampi(z, -2, nz + 1), nz) * plane; };
     auto fetch_phi = [&](int z, float *v) {
-        const float *src = phi + (long long)refl101(clampi(z, -2, nz + 1), nz) * plane;
+        const float *src = phi_plane(z);
 #pragma unroll
         for (int e = 0; e < NPE; ++e) v[e] = __ldg(src + poff[e]);
     };
@@ -933,6 +984,26 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
 #pragma unroll
         for (int e = 0; e < NPE; ++e)
             if ((int)threadIdx.x + e * kZThreads < PH * PW) dst[threadIdx.x + e * kZThreads] = v[e];
+    };
+    auto issue_phi = [&](int z, float *dst) {
+        const float *src = phi_plane(z);
+#pragma unroll
+        for (int e = 0; e < NPE; ++e)
+            if ((int)threadIdx.x + e * kZThreads < PH * PW)
+                cp_async4(dst + threadIdx.x + e * kZThreads, src + (unsigned)poff[e], true);
+    };
+    // (a, b) plane s of the chunk (z = z0 - R + s) at this thread's column; zero outside the
+    // brick and past the chunk: a load (R <= 6) or a copy into a staging slot (R >= 8)
+    const long long cab = (long long)min(y, ny - 1) * px + min(x, nx - 1);
+    const float2 *src = B.abxy + (DEEP ? 0 : cab);
+    const Off cabo = DEEP ? (Off)cab : (Off)0;
+    auto ab_ok = [&](int s) { return active && s < nplanes && (unsigned)(z0 - R + s) < (unsigned)nz; };
+    auto load_ab = [&](int s) -> float2 {
+        return ab_ok(s) ? __ldg(src + (cabo + (Off)(z0 - R + s) * pplane)) : make_float2(0.f, 0.f);
+    };
+    auto issue_ab = [&](int s, float2 *slot) {
+        const bool ok = ab_ok(s);
+        cp_async8(slot + threadIdx.x, src + (ok ? cabo + (Off)(z0 - R + s) * pplane : (Off)0), ok);
     };
     // unit normals of one plane from phi planes pm, pc, pp of the ring; the
     // central differences' factor 1/2 cancels: d / (|d| + 2e-10) = (d/2) / (|d/2| + 1e-10)
@@ -952,36 +1023,41 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
             }
         }
     };
-    auto copy_normals = [&](const float *src, float *dst) {
+    // unit normals of two consecutive planes c, c + 1 from phi planes c - 1 .. c + 2, with
+    // packed arithmetic (per lane the operations of normals(), bit for bit)
+    auto normals2 = [&](const float *pm, const float *pc, const float *pp, const float *pq, float *dc, float *dp) {
 #pragma unroll
         for (int e = 0; e < NNE; ++e) {
             const int i = threadIdx.x + e * kZThreads;
             if (i < NH * NW) {
-                dst[i] = src[i];
-                dst[NH * NW + i] = src[NH * NW + i];
-                dst[2 * NH * NW + i] = src[2 * NH * NW + i];
+                const int o = noff[e];
+                const float2 gx = f2sub(make_float2(pc[o + 1], pp[o + 1]), make_float2(pc[o - 1], pp[o - 1]));
+                const float2 gy = f2sub(make_float2(pc[o + PW], pp[o + PW]), make_float2(pc[o - PW], pp[o - PW]));
+                const float2 gz = f2sub(make_float2(pp[o], pq[o]), make_float2(pm[o], pc[o]));
+                const float2 ss = __ffma2_rn(gz, gz, __ffma2_rn(gy, gy, f2mul(gx, gx)));
+                const float2 r = f2add(make_float2(sqrt_approx(ss.x), sqrt_approx(ss.y)), f2v(2e-10f));
+                const float2 inv = make_float2(rcp_approx(r.x), rcp_approx(r.y));
+                const float2 nx2 = f2mul(gx, inv), ny2 = f2mul(gy, inv), nz2 = f2mul(gz, inv);
+                dc[i] = nx2.x;
+                dc[NH * NW + i] = ny2.x;
+                dc[2 * NH * NW + i] = nz2.x;
+                dp[i] = nx2.y;
+                dp[NH * NW + i] = ny2.y;
+                dp[2 * NH * NW + i] = nz2.y;
             }
         }
     };
-    auto phi_at = [&](int r) { return sphi + ((r + kZPhiRing) & (kZPhiRing - 1)) * PPL; };
-    auto nrm_at = [&](int r) { return snrm + ((r + kZNrmRing) & (kZNrmRing - 1)) * NPL; };
-
-    // prologue: phi planes z0-2 .. z0+3, normals z0-1 .. z0+2 (physical mapping at the faces)
-    {
-        float pv[NPE];
-        for (int r = -2; r <= 3; ++r) {
-            fetch_phi(z0 + r, pv);
-            store_phi(phi_at(r), pv);
+    auto copy_normals = [&](const float *from, float *dst) {
+#pragma unroll
+        for (int e = 0; e < NNE; ++e) {
+            const int i = threadIdx.x + e * kZThreads;
+            if (i < NH * NW) {
+                dst[i] = from[i];
+                dst[NH * NW + i] = from[NH * NW + i];
+                dst[2 * NH * NW + i] = from[2 * NH * NW + i];
+            }
         }
-    }
-    __syncthreads();
-    for (int r = -1; r <= 2; ++r) {
-        const int q = refl101(clampi(z0 + r, -1, nz), nz) - z0;  // physical plane, relative
-        normals(phi_at(q - 1), phi_at(q), phi_at(q + 1), nrm_at(r));
-    }
-    float pva[NPE], pvb[NPE];
-    fetch_phi(z0 + 4, pva);
-    fetch_phi(z0 + 5, pvb);
+    };
 
     // K*1 = p_x p_y p_z; with R = 0 (the Eq. (15) form, sigma_2 = 0) the data terms
     // take no convolution and K*1 is 1
@@ -991,106 +1067,165 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
     const float eps = B.eps, eps_pi = eps * INV_PI, eps2 = eps * eps;
     const float mu = B.mu, nu = B.nu, dt = B.dt;
-    const ImgT *img = reinterpret_cast<const ImgT *>(B.img) + col;
-    float *phi_out = (par ? B.phi[0] : B.phi[1]) + col;
-    float *q_out = (par ? B.q[0] : B.q[1]) + col;
+    const ImgT *img = reinterpret_cast<const ImgT *>(B.img) + colp;
+    float *phi_out = (par ? B.phi[0] : B.phi[1]) + colp;
+    float *q_out = (par ? B.q[0] : B.q[1]) + colp;
     float *const dump = B.dump;
-    const long long n = plane * nz;
-
-    // (a, b) plane r = -R + s of the chunk, s = 0 .. nplanes-1; zero outside the brick
-    const float2 *src = B.abxy + (long long)min(y, ny - 1) * px + min(x, nx - 1);
-    auto load = [&](int s) -> float2 {
-        const int zi = z0 - R + s;
-        return (active && s < nplanes && (unsigned)zi < (unsigned)nz) ? __ldg(src + (long long)zi * pplane)
-                                                                       : make_float2(0.f, 0.f);
+    const long long n = (long long)plane * nz;
+    // the centred image and p_z at output plane r (unused values past the chunk: 0 and 1)
+    auto img_at = [&](int r) -> float {
+        return (active && r < nout) ? centred(img, (long long)(colo + (Off)(z0 + r) * plane), inv_s, nms) : 0.f;
     };
+    auto pz_at = [&](int r) -> float { return (R == 0 || r >= nout) ? 1.f : __ldg(profz + r); };
+
+    // prologue: phi planes z0-2 .. z0+3 (R <= 6; z0+4, z0+5 in registers) or z0-2 .. z0+7 and
+    // (a, b) planes s = 2R+2 .. 2R+5 (R >= 8, copies); the register ring's planes s = 0 .. 2R+1
+    // and the image of planes z0 .. z0+NIV-1
+    float pva[NPE], pvb[NPE];
+    if constexpr (DEEP) {
+#pragma unroll 1
+        for (int r = -2; r <= 7; ++r) issue_phi(z0 + r, phi_at(r));
+#pragma unroll
+        for (int j = 2 * R + 2; j < 2 * R + 6; ++j) issue_ab(j, ab_at(j));
+        cp_async_commit();
+    } else {
+#pragma unroll 1
+        for (int r = -2; r <= 3; ++r) {
+            fetch_phi(z0 + r, pva);
+            store_phi(phi_at(r), pva);
+        }
+    }
     float2 ring[M];
 #pragma unroll
-    for (int s = 0; s < 2 * R + 2; ++s) ring[s] = load(s);
-    long long aoff = (long long)(z0 + R + 2) * pplane;  // offset of the next step's first (a, b) plane
-    long long zoff = (long long)z0 * plane;              // offset of the step's first output plane
-    float iv0 = active ? centred(img, (long long)z0 * plane, inv_s, nms) : 0.f;
-    float iv1 = (active && nout > 1) ? centred(img, (long long)(z0 + 1) * plane, inv_s, nms) : 0.f;
-    // p_z of the step's two planes, loaded a step ahead like the image
-    float kz0 = R == 0 ? 1.f : __ldg(profz), kz1 = R == 0 || nout < 2 ? 1.f : __ldg(profz + 1);
+    for (int s = 0; s < 2 * R + 2; ++s) ring[s] = load_ab(s);
+    float iv[NIV], kz[NIV];
+#pragma unroll
+    for (int j = 0; j < NIV; ++j) {
+        iv[j] = img_at(j);
+        kz[j] = pz_at(j);
+    }
+    if constexpr (DEEP) cp_async_wait0();
+    __syncthreads();
+#pragma unroll 1
+    for (int r = -1; r <= 2; ++r) {
+        const int q = refl101(clampi(z0 + r, -1, nz), nz) - z0;  // physical plane, relative
+        normals(phi_at(q - 1), phi_at(q), phi_at(q + 1), nrm_at(r));
+    }
+    if constexpr (!DEEP) {
+        fetch_phi(z0 + 4, pva);
+        fetch_phi(z0 + 5, pvb);
+    }
 
+    Off zoff = colo + (Off)z0 * plane;            // offset of the step's first output plane
+    Off aoff = (Off)(z0 + R + 2) * pplane;        // offset of the next step's first (a, b) plane (R <= 6)
     for (int base = 0; 2 * base < nout; base += SPB) {
 #pragma unroll
         for (int kk = 0; kk < SPB; ++kk) {
             const int k = base + kk;
-            const int r0 = 2 * k;          // relative output plane
+            const int r0 = 2 * k;  // relative output plane
             if (r0 < nout) {
                 const int zo = z0 + r0;
-                // the next step's (a, b) planes s = r0 + 2R + 2, + 3 (z = zo + R + 2, + 3): from a
-                // running offset at radius <= 6 (measured faster there; slower in the 128-register
-                // variants of radius >= 8, which keep the per-plane offsets)
-                if constexpr (R <= 6) {
+                // the next step's (a, b) planes s = r0 + 2R + 2, + 3 (z = zo + R + 2, + 3) and phi
+                if constexpr (DEEP) {
+                    issue_phi(zo + 8, phi_at(2 * kk + 8));
+                    issue_phi(zo + 9, phi_at(2 * kk + 9));
+                    issue_ab(r0 + 2 * R + 6, ab_at(2 * kk + 2 * R + 6));
+                    issue_ab(r0 + 2 * R + 7, ab_at(2 * kk + 2 * R + 7));
+                    cp_async_commit();
+                    cp_async_wait2();  // this thread's copies of two steps ago have landed
+                    ring[(2 * kk + 2 * R + 2) % M] = ab_at(2 * kk + 2 * R + 2)[threadIdx.x];
+                    ring[(2 * kk + 2 * R + 3) % M] = ab_at(2 * kk + 2 * R + 3)[threadIdx.x];
+                } else {
                     const bool in2 = active && r0 + 2 < nout && zo + R + 2 < nz;
                     const bool in3 = active && r0 + 3 < nout && zo + R + 3 < nz;
                     ring[(2 * kk + 2 * R + 2) % M] = in2 ? __ldg(src + aoff) : make_float2(0.f, 0.f);
                     ring[(2 * kk + 2 * R + 3) % M] = in3 ? __ldg(src + aoff + pplane) : make_float2(0.f, 0.f);
                     aoff += 2 * pplane;
-                } else {
-                    ring[(2 * kk + 2 * R + 2) % M] = load(r0 + 2 * R + 2);
-                    ring[(2 * kk + 2 * R + 3) % M] = load(r0 + 2 * R + 3);
+                    store_phi(phi_at(2 * kk + 4), pva);
+                    store_phi(phi_at(2 * kk + 5), pvb);
+                    fetch_phi(zo + 6, pva);
+                    fetch_phi(zo + 7, pvb);
                 }
-                store_phi(phi_at(2 * kk + 4), pva);
-                store_phi(phi_at(2 * kk + 5), pvb);
-                fetch_phi(zo + 6, pva);
-                fetch_phi(zo + 7, pvb);
-                const float im0 = iv0, im1 = iv1, pz0 = kz0, pz1 = kz1;
-                if constexpr (R <= 6) {
-                    if (active && r0 + 2 < nout) iv0 = centred(img, zoff + 2 * plane, inv_s, nms);
-                    if (active && r0 + 3 < nout) iv1 = centred(img, zoff + 3 * plane, inv_s, nms);
-                } else {
-                    if (active && r0 + 2 < nout) iv0 = centred(img, (long long)(zo + 2) * plane, inv_s, nms);
-                    if (active && r0 + 3 < nout) iv1 = centred(img, (long long)(zo + 3) * plane, inv_s, nms);
-                }
-                if (R != 0 && r0 + 2 < nout) kz0 = __ldg(profz + r0 + 2);
-                if (R != 0 && r0 + 3 < nout) kz1 = __ldg(profz + r0 + 3);
+                const float im0 = iv[(2 * kk) % NIV], im1 = iv[(2 * kk + 1) % NIV];
+                const float pz0 = kz[(2 * kk) % NIV], pz1 = kz[(2 * kk + 1) % NIV];
+                iv[(2 * kk) % NIV] = img_at(r0 + NIV);
+                iv[(2 * kk + 1) % NIV] = img_at(r0 + NIV + 1);
+                kz[(2 * kk) % NIV] = pz_at(r0 + NIV);
+                kz[(2 * kk + 1) % NIV] = pz_at(r0 + NIV + 1);
                 __syncthreads();
+                if (zo + 4 < nz) {
+                    normals2(phi_at(2 * kk + 2), phi_at(2 * kk + 3), phi_at(2 * kk + 4), phi_at(2 * kk + 5),
+                             nrm_at(2 * kk + 3), nrm_at(2 * kk + 4));
+                } else {
 #pragma unroll
-                for (int c = 3; c <= 4; ++c) {
-                    if (zo + c < nz)
-                        normals(phi_at(2 * kk + c - 1), phi_at(2 * kk + c), phi_at(2 * kk + c + 1), nrm_at(2 * kk + c));
-                    else if (zo + c == nz)
-                        copy_normals(nrm_at(2 * kk + c - 2), nrm_at(2 * kk + c));
+                    for (int c = 3; c <= 4; ++c) {
+                        if (zo + c < nz)
+                            normals(phi_at(2 * kk + c - 1), phi_at(2 * kk + c), phi_at(2 * kk + c + 1),
+                                    nrm_at(2 * kk + c));
+                        else if (zo + c == nz)
+                            copy_normals(nrm_at(2 * kk + c - 2), nrm_at(2 * kk + c));
+                    }
                 }
                 if (active) {
+                    // outputs zo and zo + 1 together: lane c of every float2 below is plane zo + c
+                    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        if (c == 1 && r0 + 1 >= nout) break;
-                        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int kt = 0; kt < T; ++kt) acc = f2fma(t.g[kt], ring[(2 * kk + c + kt) % M], acc);
-                        const float im = c ? im1 : im0;
-                        float g;
-                        if constexpr (R == 0) {  // Eq. (15), sigma_2 = 0: the ring holds (f1, f2)
-                            const float d1 = im - acc.x, d2 = im - acc.y;
-                            g = s2 * (l1 * (d1 * d1) - l2 * (d2 * d2));
-                        } else {  // Li's data terms from K*a, K*b
-                            const float K1 = pxy * (c ? pz1 : pz0);
-                            g = s2 * (l12 * K1 * (im * im) - 2.f * im * acc.x + acc.y);
-                        }
-                        const float *p0 = phi_at(2 * kk + c);
-                        const int pc0 = (ty + 2) * PW + tx + 2;
-                        const float ph = p0[pc0];
-                        const float lap = (p0[pc0 + 1] + p0[pc0 - 1] - 2.f * ph) + (p0[pc0 + PW] + p0[pc0 - PW] - 2.f * ph) +
-                                          (phi_at(2 * kk + c + 1)[pc0] + phi_at(2 * kk + c - 1)[pc0] - 2.f * ph);
-                        const int nc0 = (ty + 1) * NW + tx + 1;
-                        const float *nn = nrm_at(2 * kk + c);
-                        const float kap = ((nn[nc0 + 1] - nn[nc0 - 1]) + (nn[NH * NW + nc0 + NW] - nn[NH * NW + nc0 - NW]) +
-                                           (nrm_at(2 * kk + c + 1)[2 * NH * NW + nc0] -
-                                            nrm_at(2 * kk + c - 1)[2 * NH * NW + nc0])) * 0.5f;
-                        const float del = eps_pi * rcp_approx(eps2 + ph * ph);  // Eq. (14)
-                        const float pn = ph + dt * (mu * (lap - kap) + del * (nu * kap - g));
-                        const long long qz = R <= 6 ? zoff + c * plane : (long long)(zo + c) * plane;
-                        phi_out[qz] = pn;
-                        q_out[qz] = heaviside_q_fast(pn, eps);
-                        if (dump) {
-                            dump[2 * n + col + qz] = g;
-                            dump[3 * n + col + qz] = kap;
-                            dump[4 * n + col + qz] = lap;
+                    for (int kt = 0; kt < T; ++kt) {
+                        a0 = f2fma(t.g[kt], ring[(2 * kk + kt) % M], a0);
+                        a1 = f2fma(t.g[kt], ring[(2 * kk + 1 + kt) % M], a1);
+                    }
+                    const float2 im = make_float2(im0, im1);
+                    float2 g;
+                    if constexpr (R == 0) {  // Eq. (15), sigma_2 = 0: the ring holds (f1, f2)
+                        const float2 d1 = f2sub(im, make_float2(a0.x, a1.x)), d2 = f2sub(im, make_float2(a0.y, a1.y));
+                        g = f2mul(f2v(s2), __ffma2_rn(f2v(l1), f2mul(d1, d1), f2mul(f2v(-l2), f2mul(d2, d2))));
+                    } else {  // Li's data terms from K*a, K*b
+                        const float2 K1 = f2mul(f2v(pxy), make_float2(pz0, pz1));
+                        const float2 t1 = f2mul(f2mul(f2v(l12), K1), f2mul(im, im));
+                        const float2 t2 = __ffma2_rn(f2mul(f2v(-2.f), im), make_float2(a0.x, a1.x), t1);
+                        g = f2mul(f2v(s2), f2add(t2, make_float2(a0.y, a1.y)));
+                    }
+                    const int pc0 = (ty + 2) * PW + tx + 2;
+                    const float *pm = phi_at(2 * kk - 1), *p0 = phi_at(2 * kk), *p1 = phi_at(2 * kk + 1),
+                                *pp = phi_at(2 * kk + 2);
+                    const float2 ph = make_float2(p0[pc0], p1[pc0]);
+                    const float2 m2ph = f2mul(f2v(-2.f), ph);
+                    const float2 lap =
+                        f2add(f2add(f2add(f2add(make_float2(p0[pc0 + 1], p1[pc0 + 1]), make_float2(p0[pc0 - 1], p1[pc0 - 1])), m2ph),
+                                    f2add(f2add(make_float2(p0[pc0 + PW], p1[pc0 + PW]), make_float2(p0[pc0 - PW], p1[pc0 - PW])), m2ph)),
+                              f2add(f2add(make_float2(p1[pc0], pp[pc0]), make_float2(pm[pc0], p0[pc0])), m2ph));
+                    const int nc0 = (ty + 1) * NW + tx + 1;
+                    const float *nm = nrm_at(2 * kk - 1), *n0 = nrm_at(2 * kk), *n1 = nrm_at(2 * kk + 1),
+                                *np1 = nrm_at(2 * kk + 2);
+                    constexpr int NZ = 2 * NH * NW;
+                    const float2 kap = f2mul(
+                        f2add(f2add(f2sub(make_float2(n0[nc0 + 1], n1[nc0 + 1]), make_float2(n0[nc0 - 1], n1[nc0 - 1])),
+                                    f2sub(make_float2(n0[NH * NW + nc0 + NW], n1[NH * NW + nc0 + NW]),
+                                          make_float2(n0[NH * NW + nc0 - NW], n1[NH * NW + nc0 - NW]))),
+                              f2sub(make_float2(n1[NZ + nc0], np1[NZ + nc0]), make_float2(nm[NZ + nc0], n0[NZ + nc0]))),
+                        f2v(0.5f));
+                    const float2 den = __ffma2_rn(ph, ph, f2v(eps2));
+                    const float2 del = f2mul(f2v(eps_pi), make_float2(rcp_approx(den.x), rcp_approx(den.y)));  // Eq. (14)
+                    const float2 pn = __ffma2_rn(
+                        f2v(dt), __ffma2_rn(del, __ffma2_rn(f2v(nu), kap, make_float2(-g.x, -g.y)),
+                                            f2mul(f2v(mu), f2sub(lap, kap))),
+                        ph);
+                    const float2 qn = heaviside_q_fast2(pn, eps);
+                    phi_out[zoff] = pn.x;
+                    q_out[zoff] = qn.x;
+                    if (r0 + 1 < nout) {
+                        phi_out[zoff + plane] = pn.y;
+                        q_out[zoff + plane] = qn.y;
+                    }
+                    if (dump) {
+                        const long long q0 = colp + (long long)zoff, q1 = q0 + (long long)plane;
+                        dump[2 * n + q0] = g.x;
+                        dump[3 * n + q0] = kap.x;
+                        dump[4 * n + q0] = lap.x;
+                        if (r0 + 1 < nout) {
+                            dump[2 * n + q1] = g.y;
+                            dump[3 * n + q1] = kap.y;
+                            dump[4 * n + q1] = lap.y;
                         }
                     }
                 }
@@ -1098,6 +1233,7 @@ __global__ void __launch_bounds__(kZThreads, R <= 6 ? 3 : 2) k_tb_z(GroupArgs G,
             }
         }
     }
+    if constexpr (DEEP) cp_async_wait0();  // no copy into this CTA's shared memory outlives it
 }
 
 // ------------------------------------------------------------ launchers

@@ -16,17 +16,17 @@ cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStr
         t.R = 0;
         t.g[0] = 1.f;
     }
-    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem(), s>>>(G, tap_pairs(t));
+    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem<R>(), s>>>(G, tap_pairs(t));
     return cudaGetLastError();
 }
 template <int R>
 cudaError_t prepare_bz_i() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem())) !=
+    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>())) !=
         cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem())) !=
+    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>())) !=
         cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tb_z<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem());
+    return cudaFuncSetAttribute(k_tb_z<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>());
 }
 template <int R>
 cudaError_t launch_bz_i(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
@@ -82,6 +82,10 @@ bool tiled_supports(int R) {
 }
 
 int tiled_pitch(int nx) { return (nx + tiled::kZX - 1) / tiled::kZX * tiled::kZX; }
+
+bool tiled_fits(long long nx, long long ny, long long nz) {
+    return (long long)tiled_pitch((int)nx) * ny * nz < (1LL << 32);
+}
 
 cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s) {
     tiled::k_q_init<<<1216, 256, 0, s>>>(phi, q, n, eps);

@@ -14,10 +14,10 @@ CUH = os.path.join(ROOT, "paper_2404_02813_gb300", "csrc", "rsf_tiled.cuh")
 
 def kernel_coefficients():
     src = open(CUH).read()
-    body = src[src.index("float atan01_pi(float x)"):]
-    body = body[:body.index("return x * p;")]
+    body = src[src.index("constexpr float kAtanPi[9]"):]
+    body = body[:body.index("};")]
     vals = [float(v) for v in re.findall(r"([-+]?\d\.\d+e[-+]\d+)f", body)]
-    return np.array(vals[::-1], dtype=np.float32)  # Horner runs from c8 down to c0
+    return np.array(vals[::-1], dtype=np.float32)  # the array runs from c8 down to c0 (Horner order)
 
 
 def test_kernel_constants_match_the_derivation():
