@@ -368,26 +368,26 @@ def serve_params(spec):
     return dict(sigma=spec.sigma, eps=1.0, lambda1=1.0, lambda2=2.0, nu=0.004 * P * P, mu=1.0, dt=0.1)
 
 
-def run_serve(args, rank, world, local):
-    """Poisson arrivals of brick requests at several rates through rsf_submit (FP16
-    storage, 150 GB budget), against sequential plain FP32 solves of the same requests
-    (FIFO single-server latencies from their measured service times)."""
+def serve_pool(npool=32):
+    """Request images and their specs (spawn-context process pool: no CUDA state is shared)."""
     from concurrent.futures import ProcessPoolExecutor
     from multiprocessing import get_context
     from paper_2404_02813_gb300 import synth
-    npool = 32
     specs = synth.serve_request_specs(npool)
     with ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)), mp_context=get_context("spawn")) as ex:
         pool = list(ex.map(_serve_worker, list(enumerate(specs)), chunksize=1))
+    return specs, pool
+
+
+def serve_measure(local, specs, pool, rates, nreq, seed=5005):
+    """Poisson arrivals of `nreq` brick requests per rate through rsf_submit (FP16 storage,
+    150 GB budget), against sequential plain FP32 solves of the same requests (FIFO
+    single-server latencies from their measured service times)."""
     import torch
     from paper_2404_02813_gb300 import rsf
-    torch.cuda.set_device(local)
-    if rank != 0:
-        return
+    npool = len(pool)
     dev = [(torch.from_numpy(v).cuda(), torch.from_numpy(p).cuda()) for v, p in pool]
-    rng = np.random.default_rng(5005)
-    rates = [float(r) for r in args.rates.split(",")]
-    nreq = args.requests
+    rng = np.random.default_rng(seed)
     # the request list: pool volume, and a fresh iteration count per request
     reqs = [(int(rng.integers(0, npool)), int(rng.integers(50, 501))) for _ in range(nreq)]
     work = [dev[k][0].numel() * it for k, it in reqs]
@@ -436,15 +436,115 @@ def run_serve(args, rank, world, local):
             "p50_s": st["latency_p50_s"], "p99_s": st["latency_p99_s"],
             "sequential_fp32": {"gvox_it_s": sum(work) / sum(service) / 1e9,
                                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))}})
+    return results
+
+
+def run_serve(args, rank, world, local):
+    specs, pool = serve_pool()
+    import torch
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return
+    rates = [float(r) for r in args.rates.split(",")]
+    results = serve_measure(local, specs, pool, rates, args.requests)
     best = max(r["gvox_it_s"] for r in results)
     line = {"metric": "GVoxel-iterations/s", "value": best, "unit": "GVoxel-iterations/s", "n_gpus": 1,
             "steps": len(rates), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 compute, f16 storage", "data": "synthetic (light-sheet, micro-CT and milling-like bricks)",
-            "config": {"workload": f"serve: {nreq} brick requests per rate, Poisson arrivals, core edges log-uniform "
-                                   "32-256 + 3 sigma halo, sigma in {2,3,4,6}, iterations U{50..500}, FP16 storage, "
-                                   "150 GB budget, 64 slots; request images drawn from a pool of 32",
+            "config": {"workload": f"serve: {args.requests} brick requests per rate, Poisson arrivals, core edges "
+                                   "log-uniform 32-256 + 3 sigma halo, sigma in {2,3,4,6}, iterations U{50..500}, FP16 "
+                                   "storage, 150 GB budget, 64 slots; request images drawn from a pool of 32",
                        "rates": results}}
     print(json.dumps(line), flush=True)
+
+
+def batched_measure(local, bricks, params, iters, steps=2):
+    """Bricks advanced together by rsf_evolve_batch (FP32, autotuned, CUDA graph) against the
+    same bricks solved one after another by rsf_evolve; GVoxel-iterations/s of padded voxels."""
+    import torch
+    from paper_2404_02813_gb300 import rsf
+    dev = [(torch.from_numpy(v).cuda(), torch.from_numpy(p).cuda()) for v, p in bricks]
+    items = [(v, p, params, iters, torch.empty_like(p)) for v, p in dev]
+    padded = sum(v.numel() for v, _ in dev)
+    ctx = rsf.Context(local)
+    ctx.set_option(rsf.OPT_AUTOTUNE, 1)
+    stream = torch.cuda.ExternalStream(ctx.stream_handle)
+    ctx.evolve_batch(items)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.evolve_batch(items)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batched = padded * iters * steps / (e0.elapsed_time(e1) / 1e3) / 1e9
+    outs = [torch.empty_like(p) for _, p in dev]
+    for (v, p), o in zip(dev, outs):
+        ctx.evolve(v, p, params, iters, out=o)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for (v, p), o in zip(dev, outs):
+        ctx.evolve(v, p, params, iters, out=o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain = padded * iters / (e0.elapsed_time(e1) / 1e3) / 1e9
+    ctx.close()
+    return {"bricks": len(bricks), "padded_voxels": int(padded), "iterations": iters,
+            "batched_gvox_it_s": batched, "sequential_plain_gvox_it_s": plain, "ratio": batched / plain}
+
+
+def parity_report(local, ls_vol, ls_phi0, ls_params):
+    """Error of the GPU against the FP64 oracle after each configuration's own iteration count.
+
+    Per case: max |phi_gpu - phi_oracle| and the fraction of voxels whose sign differs, beside
+    the oracle's own envelope -- the oracle from phi0 moved by a relative 2^-24 (a random sign
+    per voxel) against the oracle from phi0.  Near a vanishing gradient the unit normal, hence
+    one step, is discontinuous in phi, so after many iterations the envelope sets the scale on
+    which the GPU's distance from the oracle is read (the per-iteration parity tests bound the
+    step itself).  The oracle runs in its OpenMP build on all host cores."""
+    import oracle
+    import torch
+    from paper_2404_02813_gb300 import rsf, synth
+    cases = []
+    vol = synth.tree_volume_u8()
+    cases.append(("tree64 (64^3 uint8 vessel tree, box phi0, sigma 3)", vol, synth.box_phi0(vol.shape, 32),
+                  synth.RSFParams().as_dict(), 50, ["f32", "f16", "bf16"]))
+    c = 128
+    o = [(n - c) // 2 for n in ls_vol.shape]
+    crop = tuple(slice(a, a + c) for a in o)
+    cases.append((f"lightsheet 128^3 sub-brick (offset {o[::-1]}) of the 512^3 volume, sigma 3",
+                  np.ascontiguousarray(ls_vol[crop]), np.ascontiguousarray(ls_phi0[crop]), ls_params, 200, ["f32"]))
+    mvol = synth.MillingField(extent_xyz=(1024, 1024, 1024)).box((448, 448, 448), (c, c, c))
+    cases.append(("milling 128^3 sub-brick (offset 448^3) of the 1024^3 field, sigma 3", mvol,
+                  synth.mean_rule_phi0(mvol), synth.RSFParams().as_dict(), 300, ["f16", "bf16", "f32"]))
+    rng = np.random.default_rng(24)
+    ctx = rsf.Context(local)
+    out = {}
+    for name, vol, phi0, p, iters, storages in cases:
+        I = vol.astype(np.float64)
+        P = phi0.astype(np.float64)
+        t0 = time.perf_counter()
+        ref = oracle.evolve(I, P, p, iters, omp=True)
+        env = oracle.evolve(I, P * (1.0 + 2.0 ** -24 * np.where(rng.random(P.shape) < 0.5, -1.0, 1.0)), p, iters,
+                            omp=True)
+        t_or = time.perf_counter() - t0
+
+        def cmp(a):
+            return {"max_abs_dphi": float(np.abs(a - ref).max()),
+                    "sign_disagreement": float(np.mean(np.sign(a) != np.sign(ref)))}
+
+        ent = {"case": name, "iterations": iters, "oracle_envelope": cmp(env), "oracle_s": round(t_or, 2)}
+        v = torch.from_numpy(vol).cuda()
+        ph = torch.from_numpy(phi0).cuda()
+        for st in storages:
+            ctx.set_storage(st)
+            ent[st] = cmp(ctx.evolve(v, ph, p, iters).cpu().numpy().astype(np.float64))
+        ctx.set_storage("f32")
+        out[name.split(" ")[0]] = ent
+    ctx.close()
+    out["note"] = ("GPU (per storage) and the oracle from the same phi0 after the configuration's iterations; the "
+                   "envelope is the oracle against itself from phi0 perturbed by a relative 2^-24")
+    return out
 
 
 def run_init(args, rank, world, local):
@@ -487,6 +587,60 @@ def run_init(args, rank, world, local):
                                       "note": "phi0 = 0 by marching tetrahedra, count + emit into host memory"}}}
     print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def default_extras(args, local, ctx, stream, v, ph0, vol, phi0, params, iters):
+    """The default line's untimed companions; a failure is recorded in its key, not raised."""
+    import torch
+    out = {}
+
+    def guarded(key, fn):
+        t0 = time.perf_counter()
+        try:
+            out[key] = fn()
+        except Exception as e:  # the headline stands whatever happens here
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+        print(f"bench: {key} in {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+
+    def storages():
+        res = {}
+        for st in ("f16", "bf16"):
+            ctx.set_storage(st)
+            o = torch.empty_like(ph0)
+            ctx.evolve(v, ph0, params, iters, out=o)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                ctx.evolve(v, ph0, params, iters, out=o)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[st] = {"gvox_it_s": vol.size * iters * 2 / (e0.elapsed_time(e1) / 1e3) / 1e9}
+        ctx.set_storage("f32")
+        res["note"] = "the same volume, parameters and iterations with (a, b) stored in 16 bits; 2 steps each"
+        return res
+
+    def batched():
+        bricks, bparams, biters = make_bricks(64, 0)
+        r = batched_measure(local, bricks, bparams, biters)
+        r["note"] = ("64 of the bricks256 workload's halo-padded uint16 bricks (core edges U[64,192], halo 12), "
+                     "sigma 4, 150 iterations, FP32: one batched launch per kernel per iteration (CUDA graph, "
+                     "autotuned z chunk) against rsf_evolve brick after brick")
+        return r
+
+    def serving():
+        specs, pool = serve_pool(32)
+        r = serve_measure(local, specs, pool, [100.0], 150)[0]
+        r["note"] = ("150 requests at 100 req/s (Poisson), request images from a pool of 32 (core edges log-uniform "
+                     "32-256 + 3 sigma halo, sigma in {2,3,4,6}, iterations U{50..500}), FP16 storage, 150 GB "
+                     "budget; sequential_fp32: the same requests solved one after another by rsf_evolve (FIFO)")
+        return r
+
+    guarded("storage_variants", storages)
+    guarded("parity", lambda: parity_report(local, vol, phi0, params))
+    guarded("batched", batched)
+    guarded("serving", serving)
+    return out
 
 
 def workload_desc(name, vol, params, iters):
@@ -755,6 +909,13 @@ def main():
                            "envelope is FP32 against FP32 from a phi0 perturbed by one ulp per voxel"}
         del ref32, ref32p, ph0p, up
 
+    # reported beside the headline, untimed relative to it: 16-bit storage on the same volume,
+    # the error against the oracle per configuration, batched bricks, one serving rate
+    extras = {}
+    if (args.workload == "lightsheet512" and world == 1 and rank == 0 and not args.lean and args.size is None
+            and not args.curtain and args.storage == "f32" and force == "li"):
+        extras = default_extras(args, local, ctx, stream, v, ph0, vol, phi0, params, iters)
+
     if rank == 0:
         peak, peak_kind = peaks()
         dom = max(prof, key=lambda k: prof[k][1])
@@ -796,7 +957,8 @@ def main():
                               if args.curtain else {}),
                            force={"li": "li (e_i with K*1, K*f_i)", "eq15": "eq15 (paper's Eq. 15, sigma_2 = 0)"}[force],
                            parallelism=f"replicas{world}" if world > 1 else "single-gpu"),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "issue" if issue is not None and issue["frac"] > achieved / peak else "hbm",
+                         "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                          "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic": traffic, "algo_bytes_per_launch": algo,
@@ -817,6 +979,7 @@ def main():
             line["segmentation"] = seg
         if seg_seeded is not None:
             line["segmentation_seeded"] = seg_seeded
+        line.update(extras)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(vol, phi0, params, force=force)
             line["cpu_baseline_omp"] = cpu_baseline_omp(vol, phi0, params, force=force)

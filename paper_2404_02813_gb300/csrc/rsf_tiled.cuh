@@ -911,6 +911,7 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 template <int R, class ImgT>
 __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(GroupArgs G, TapPairs t) {
     constexpr bool DEEP = tbz_deep<R>();
+    constexpr bool PHI_ASYNC = DEEP;  // phi planes copied into the ring two steps ahead (cp.async)
     using Off = typename std::conditional<DEEP, unsigned, long long>::type;  // offsets within a field
     constexpr int NIV = DEEP ? 4 : 2;  // image and p_z registers: planes zo .. zo + NIV - 1
     constexpr int T = 2 * R + 1;
@@ -986,11 +987,11 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
             if ((int)threadIdx.x + e * kZThreads < PH * PW) dst[threadIdx.x + e * kZThreads] = v[e];
     };
     auto issue_phi = [&](int z, float *dst) {
-        const float *src = phi_plane(z);
+        const Off zb = (Off)refl101(clampi(z, -2, nz + 1), nz) * plane;
 #pragma unroll
         for (int e = 0; e < NPE; ++e)
             if ((int)threadIdx.x + e * kZThreads < PH * PW)
-                cp_async4(dst + threadIdx.x + e * kZThreads, src + (unsigned)poff[e], true);
+                cp_async4(dst + threadIdx.x + e * kZThreads, phi + (zb + (Off)poff[e]), true);
     };
     // (a, b) plane s of the chunk (z = z0 - R + s) at this thread's column; zero outside the
     // brick and past the chunk: a load (R <= 6) or a copy into a staging slot (R >= 8)
@@ -1082,11 +1083,15 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
     // (a, b) planes s = 2R+2 .. 2R+5 (R >= 8, copies); the register ring's planes s = 0 .. 2R+1
     // and the image of planes z0 .. z0+NIV-1
     float pva[NPE], pvb[NPE];
-    if constexpr (DEEP) {
+    if constexpr (PHI_ASYNC) {
 #pragma unroll 1
         for (int r = -2; r <= 7; ++r) issue_phi(z0 + r, phi_at(r));
+    }
+    if constexpr (DEEP) {
 #pragma unroll
         for (int j = 2 * R + 2; j < 2 * R + 6; ++j) issue_ab(j, ab_at(j));
+    }
+    if constexpr (PHI_ASYNC || DEEP) {
         cp_async_commit();
     } else {
 #pragma unroll 1
@@ -1104,14 +1109,14 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
         iv[j] = img_at(j);
         kz[j] = pz_at(j);
     }
-    if constexpr (DEEP) cp_async_wait0();
+    if constexpr (PHI_ASYNC || DEEP) cp_async_wait0();
     __syncthreads();
 #pragma unroll 1
     for (int r = -1; r <= 2; ++r) {
         const int q = refl101(clampi(z0 + r, -1, nz), nz) - z0;  // physical plane, relative
         normals(phi_at(q - 1), phi_at(q), phi_at(q + 1), nrm_at(r));
     }
-    if constexpr (!DEEP) {
+    if constexpr (!PHI_ASYNC) {
         fetch_phi(z0 + 4, pva);
         fetch_phi(z0 + 5, pvb);
     }
@@ -1126,13 +1131,19 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
             if (r0 < nout) {
                 const int zo = z0 + r0;
                 // the next step's (a, b) planes s = r0 + 2R + 2, + 3 (z = zo + R + 2, + 3) and phi
-                if constexpr (DEEP) {
+                if constexpr (PHI_ASYNC) {
                     issue_phi(zo + 8, phi_at(2 * kk + 8));
                     issue_phi(zo + 9, phi_at(2 * kk + 9));
+                }
+                if constexpr (DEEP) {
                     issue_ab(r0 + 2 * R + 6, ab_at(2 * kk + 2 * R + 6));
                     issue_ab(r0 + 2 * R + 7, ab_at(2 * kk + 2 * R + 7));
+                }
+                if constexpr (PHI_ASYNC || DEEP) {
                     cp_async_commit();
                     cp_async_wait2();  // this thread's copies of two steps ago have landed
+                }
+                if constexpr (DEEP) {
                     ring[(2 * kk + 2 * R + 2) % M] = ab_at(2 * kk + 2 * R + 2)[threadIdx.x];
                     ring[(2 * kk + 2 * R + 3) % M] = ab_at(2 * kk + 2 * R + 3)[threadIdx.x];
                 } else {
@@ -1141,6 +1152,8 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
                     ring[(2 * kk + 2 * R + 2) % M] = in2 ? __ldg(src + aoff) : make_float2(0.f, 0.f);
                     ring[(2 * kk + 2 * R + 3) % M] = in3 ? __ldg(src + aoff + pplane) : make_float2(0.f, 0.f);
                     aoff += 2 * pplane;
+                }
+                if constexpr (!PHI_ASYNC) {
                     store_phi(phi_at(2 * kk + 4), pva);
                     store_phi(phi_at(2 * kk + 5), pvb);
                     fetch_phi(zo + 6, pva);
@@ -1233,7 +1246,7 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
             }
         }
     }
-    if constexpr (DEEP) cp_async_wait0();  // no copy into this CTA's shared memory outlives it
+    if constexpr (PHI_ASYNC || DEEP) cp_async_wait0();  // no copy into this CTA's shared memory outlives it
 }
 
 // ------------------------------------------------------------ launchers
