@@ -297,6 +297,7 @@ def run_batch(args, rank, world, local):
     clk = clocks.stop()
     ms_max = max_over_ranks(ev0.elapsed_time(ev1), world)
     value = whole_job_rate(padded * iters * args.steps, world, ms_max / 1e3)
+    tuned = ctx.autotune_report()
     # per-kernel device time: one more step with per-launch events (direct launches)
     ctx.prof_enable(True)
     ctx.evolve_batch(items)
@@ -344,6 +345,7 @@ def run_batch(args, rank, world, local):
                          "algo_bytes_per_launch": algo, "avg_launch_ms": avg_s * 1e3, "launches": n_l,
                          "note": "per-kernel times from one extra step with per-launch events"},
             "kernels": {k: {"launches": n, "ms": round(m, 3)} for k, (n, m) in prof.items() if n},
+            "autotune": tuned,
             "clocks": clk,
             "gpu_launches": (4 * iters + 5 * nb) * args.steps,  # per brick set-up: statistics (2), q, K*I~ (2)
             "e2e": e2e,
@@ -488,9 +490,11 @@ def batched_measure(local, bricks, params, iters, steps=2):
     e1.record(stream)
     torch.cuda.synchronize()
     plain = padded * iters / (e0.elapsed_time(e1) / 1e3) / 1e9
+    tuned = ctx.autotune_report()
     ctx.close()
     return {"bricks": len(bricks), "padded_voxels": int(padded), "iterations": iters,
-            "batched_gvox_it_s": batched, "sequential_plain_gvox_it_s": plain, "ratio": batched / plain}
+            "batched_gvox_it_s": batched, "sequential_plain_gvox_it_s": plain, "ratio": batched / plain,
+            "autotune": tuned}
 
 
 def parity_report(local, ls_vol, ls_phi0, ls_params):

@@ -254,10 +254,15 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   FP32 (group A forms K*((1-H) I) and K*(1-H) as
  *                   differences, which 16-bit storage would not survive).
  *                   16-bit storage needs the tiled path.
- *   RSF_OPT_AUTOTUNE 1: rsf_evolve_batch picks the update kernel's z chunk per
- *                   brick group by timing candidates on a discarded first
- *                   iteration and remembers the choice in the context; 0
- *                   (default): a size heuristic.
+ *   RSF_OPT_AUTOTUNE 1: rsf_evolve_batch picks each brick group's launch
+ *                   shape by timing discarded first iterations, one knob after
+ *                   the other: z planes per CTA of the x/y kernels (16, 8, 32),
+ *                   the update kernel's z chunk (a size heuristic, 32, 64, 128,
+ *                   256) and the brick-to-CTA order (largest or smallest bricks
+ *                   first); the choice is remembered in the context per group
+ *                   (radius, image type, storage, form, brick count, size
+ *                   class) and listed by rsf_autotune_report.  0 (default):
+ *                   16 planes, the size heuristic, largest first.
  *   RSF_OPT_GRAPH   1 (default): rsf_evolve_batch replays its iterations from
  *                   a captured CUDA graph; 0: direct launches.
  *   RSF_OPT_SERVE_SLOTS  the most bricks the serving loop advances together
@@ -316,6 +321,18 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 rsf_status rsf_set_option(rsf_ctx *ctx, int32_t key, int64_t value);
 
 /*
+ * rsf_autotune_report -- the launch shapes the batch autotuner chose in this
+ * context (RSF_OPT_AUTOTUNE), one text line per brick group:
+ *   "<group key> zc=<z chunk> xyp=<x/y planes per CTA> order=<largest|smallest>
+ *    ms=<iteration time of the choice> default_ms=<iteration time with the
+ *    defaults>"
+ * written NUL-terminated into buf (cap bytes, truncated to fit); "" when
+ * nothing was tuned.  A tuning aid with no counterpart in the paper.
+ * Errors: RSF_E_INVAL (null context, null buffer or cap <= 0).
+ */
+rsf_status rsf_autotune_report(rsf_ctx *ctx, char *buf, int32_t cap);
+
+/*
  * Serving: continuous batching of brick requests (no counterpart in the
  * paper's method beyond its independent sub-volumes, Sec. 4.1).
  *
@@ -346,10 +363,13 @@ rsf_status rsf_set_option(rsf_ctx *ctx, int32_t key, int64_t value);
  * first poll that returns a final status (later polls: RSF_E_NOTFOUND).
  * rsf_wait blocks up to timeout_ms (< 0: no limit) for a final status, then
  * behaves as rsf_poll; on expiry it returns RSF_E_TIMEOUT and keeps the ticket.
+ * The loop advances its active bricks by dispatches of one to eight
+ * iterations: while no brick is due to finish and nothing waits in the queue,
+ * a dispatch enqueues several iterations without a host round trip.
  * rsf_cancel marks a request cancelled: it leaves the queue, or the batch at
- * the next step, and its phi_out is not written.
+ * the end of the current dispatch, and its phi_out is not written.
  * rsf_suspend marks a request for suspension (checkpointing): it leaves the
- * queue, or the batch after its current step; phi_out receives phi after the
+ * queue, or the batch at the end of the current dispatch; phi_out receives phi after the
  * iterations it completed (phi0 itself if none), their count is written to
  * *iters_done (host memory, nullable, valid until the ticket resolves), and
  * the final status is RSF_SUSPENDED.  phi and the iteration count are the

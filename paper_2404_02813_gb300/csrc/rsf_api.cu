@@ -487,6 +487,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
         b.mu = mu;
         b.dt = dt;
         b.zc = c->opt_zchunk;
+        b.xyp = rsf::kDefaultXYPlanes;
         if (b.zc <= 0) {  // enough z chunks for about 16 CTAs per SM
             int sms = 0;
             RSF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));

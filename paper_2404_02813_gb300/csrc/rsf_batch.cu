@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -83,49 +84,95 @@ rsf_status launch_all(rsf_ctx *c, const std::vector<rsf::TiledGroup> &groups, in
     return RSF_OK;
 }
 
-// Time one iteration (parity 0: reads phi[0], writes phi[1]) of `g` for each
-// candidate z chunk and keep the fastest.
-rsf_status autotune_zc(rsf_ctx *c, GroupSpec &g, int sms) {
+void set_xyp(GroupSpec &g, int xyp) {
+    for (rsf::BrickDev &b : g.bricks) b.xyp = xyp;
+}
+
+// The tuned choices on a group whose bricks are in largest-first order.
+void apply_tuned(GroupSpec &g, const TunedGroup &t) {
+    set_zc(g, t.zc);
+    set_xyp(g, t.xyp);
+    if (t.order) std::reverse(g.bricks.begin(), g.bricks.end());
+}
+
+// Device time of one iteration (parity 0: reads phi[0], writes phi[1]) of `g`, the
+// second of two back-to-back launches (the first warms caches and attributes).
+rsf_status time_iteration(rsf_ctx *c, const GroupSpec &g, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+    std::vector<GroupSpec> one{g};
+    std::vector<rsf::TiledGroup> up;
+    rsf_status st = upload_groups(c, c->desc, c->stream, one, &up);
+    if (st) return st;
+    for (int rep = 0; rep < 2; ++rep) {
+        RSF_CUDA(cudaEventRecord(e0, c->stream));
+        if ((st = launch_all(c, up, 0, nullptr))) return st;
+        RSF_CUDA(cudaEventRecord(e1, c->stream));
+    }
+    RSF_CUDA(cudaEventSynchronize(e1));
+    RSF_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    return RSF_OK;
+}
+
+// Pick the group's launch choices by timing iterations, one knob after the other from
+// the defaults: z planes per x/y CTA {16, 8, 32}, then the update kernel's z chunk
+// {size heuristic, 32, 64, 128, 256}, then the brick order (largest or smallest
+// first).  The iterations are discarded (the real first iteration rewrites their
+// outputs); the choice is cached in the context per group key.
+rsf_status autotune(rsf_ctx *c, GroupSpec &g, int sms) {
     const std::string key = group_key(g);
-    auto hit = c->tuned_zc.find(key);
-    if (hit != c->tuned_zc.end()) {
-        set_zc(g, hit->second);
+    auto hit = c->tuned.find(key);
+    if (hit != c->tuned.end()) {
+        apply_tuned(g, hit->second);
         return RSF_OK;
     }
     int maxnz = 16;
     for (const rsf::BrickDev &b : g.bricks) maxnz = std::max(maxnz, b.nz);
-    std::vector<int> cand = {default_zc(g.bricks, sms), 32, 64, 128, 256};
-    std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
     cudaEvent_t e0, e1;
     RSF_CUDA(cudaEventCreate(&e0));
     RSF_CUDA(cudaEventCreate(&e1));
-    int best = cand[0];
-    float best_ms = 1e30f;
-    for (int zc : cand) {
-        if (zc > maxnz && zc != cand[0]) continue;
-        set_zc(g, zc);
-        std::vector<GroupSpec> one{g};
-        std::vector<rsf::TiledGroup> up;
-        rsf_status st = upload_groups(c, c->desc, c->stream, one, &up);
-        if (st) return st;
-        for (int rep = 0; rep < 2; ++rep) {  // first launch warms caches and attributes
-            RSF_CUDA(cudaEventRecord(e0, c->stream));
-            if ((st = launch_all(c, up, 0, nullptr))) return st;
-            RSF_CUDA(cudaEventRecord(e1, c->stream));
+    const GroupSpec base = g;
+    rsf_status st = RSF_OK;
+    auto trial = [&](const TunedGroup &t, float *ms) {
+        GroupSpec h = base;
+        apply_tuned(h, t);
+        return time_iteration(c, h, e0, e1, ms);
+    };
+    TunedGroup best;
+    best.zc = default_zc(g.bricks, sms);
+    best.xyp = rsf::kDefaultXYPlanes;
+    float ms = 0.f;
+    if (!(st = trial(best, &ms))) {
+        best.ms = best.ms_default = ms;
+        auto consider = [&](TunedGroup cand) {
+            if (st) return;
+            if ((st = trial(cand, &ms))) return;
+            if (ms < best.ms) {
+                cand.ms = ms;
+                cand.ms_default = best.ms_default;
+                best = cand;
+            }
+        };
+        for (int xyp : {8, 32}) {
+            TunedGroup cand = best;
+            cand.xyp = xyp;
+            consider(cand);
         }
-        RSF_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        RSF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = zc;
+        for (int zc : {32, 64, 128, 256}) {
+            if (zc == best.zc || zc > maxnz) continue;
+            TunedGroup cand = best;
+            cand.zc = zc;
+            consider(cand);
+        }
+        if (g.bricks.size() > 1) {
+            TunedGroup cand = best;
+            cand.order = 1;
+            consider(cand);
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_zc(g, best);
-    c->tuned_zc[key] = best;
+    if (st) return st;
+    c->tuned[key] = best;
+    apply_tuned(g, best);
     return RSF_OK;
 }
 
@@ -217,6 +264,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         d.mu = b.mu;
         d.dt = b.dt;
         d.zc = 16;
+        d.xyp = rsf::kDefaultXYPlanes;
         rsf::Fields f;
         f.d = rsf::Dims{d.nx, d.ny, d.nz, (long long)b.nx * b.ny, n};
         f.partials = c->f.partials;
@@ -276,7 +324,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
             if (c->opt_zchunk > 0) {
                 set_zc(g, c->opt_zchunk);
             } else if (c->opt_autotune && t == 0 && !tuned_once) {
-                if ((st = autotune_zc(c, g, sms))) return st;
+                if ((st = autotune(c, g, sms))) return st;
             } else {
                 set_zc(g, default_zc(g.bricks, sms));
             }
@@ -320,5 +368,23 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         if ((st = retire(t))) return st;
     }
     RSF_CUDA(cudaStreamSynchronize(c->stream));
+    return RSF_OK;
+}
+
+extern "C" rsf_status rsf_autotune_report(rsf_ctx *c, char *buf, int32_t cap) {
+    if (!c) return fail(RSF_E_INVAL, "null context");
+    if (!buf || cap <= 0) return fail(RSF_E_INVAL, "null or empty buffer");
+    std::lock_guard<std::mutex> lk(c->mu);
+    std::string out;
+    for (const auto &kv : c->tuned) {
+        char line[256];
+        snprintf(line, sizeof line, "%s zc=%d xyp=%d order=%s ms=%.4f default_ms=%.4f\n", kv.first.c_str(),
+                 kv.second.zc, kv.second.xyp, kv.second.order ? "smallest" : "largest", kv.second.ms,
+                 kv.second.ms_default);
+        out += line;
+    }
+    const size_t n = std::min(out.size(), (size_t)cap - 1);
+    memcpy(buf, out.data(), n);
+    buf[n] = 0;
     return RSF_OK;
 }

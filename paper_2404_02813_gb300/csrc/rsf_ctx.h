@@ -21,6 +21,15 @@ struct DescBuffers {
     int cap_bricks = 0, cap_starts = 0;
 };
 
+// Launch choices the batch autotuner picked for one group key, with the measured
+// iteration times (ms: the choice, ms_default: the default choice).
+struct TunedGroup {
+    int zc = 0;     // update kernel z chunk
+    int xyp = 0;    // z planes per CTA of the x/y kernels
+    int order = 0;  // 0: largest bricks first in the CTA order, 1: smallest first
+    float ms = 0.f, ms_default = 0.f;
+};
+
 struct rsf_ctx {
     int device = 0;
     uint64_t budget = 0;
@@ -46,7 +55,7 @@ struct rsf_ctx {
     int opt_graph = 1;
     void *pool = nullptr;               // per-brick fields of rsf_evolve_batch
     size_t pool_cap = 0;
-    std::map<std::string, int> tuned_zc;  // autotuned update-kernel z chunk per group key
+    std::map<std::string, TunedGroup> tuned;  // autotuned launch choices per group key
     std::mutex alloc_mu;                // guards `used` (the serving thread allocates too)
     std::mutex serve_mu;                // guards creation of the serving loop
     void *server = nullptr;             // the serving loop (rsf_serve.cu), created by rsf_submit

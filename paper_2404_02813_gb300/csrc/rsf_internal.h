@@ -103,6 +103,7 @@ struct BrickDev {
     float *ki;              // pitched K*I~ (the centred image convolved), FP32, set once per solve
     float eps, lambda1, lambda2, nu, mu, dt;
     int zc;                 // z chunk of the update kernel
+    int xyp;                // z planes per CTA of the x/y kernels (<= 0: kDefaultXYPlanes)
     int flip;               // this brick's buffer parity is the launch parity xor flip
     float *dump;            // optional 5 * n stage fields (f1, f2, g, kappa, L)
 };
@@ -118,6 +119,8 @@ struct TiledGroup {
     const int *starts[4];   // device: per kernel, nb + 1 CTA offsets
     unsigned ncta[4];       // CTAs per kernel launch
 };
+
+constexpr int kDefaultXYPlanes = 16;
 
 // Tiled four-kernel path (rsf_tiled*.cu) for the radii it is instantiated for.
 bool tiled_supports(int R);

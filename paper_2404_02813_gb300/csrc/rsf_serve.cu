@@ -15,7 +15,10 @@
 // iteration) retires at once: its phi is copied to
 // the caller's phi_out, a host callback stamps its completion time, and its
 // memory returns to the pool in stream order, so the next admission can use
-// it.  The loop runs at most a few ticks ahead of the GPU.
+// it.  While the active set cannot change (no brick is due to finish, nothing
+// waits in the queue, nothing is to be cancelled or suspended), one dispatch
+// enqueues up to kMaxTicks ticks without a host round trip; the loop runs at
+// most kMaxAhead dispatches ahead of the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,7 +44,8 @@ using Clock = std::chrono::steady_clock;
 double now_s() { return std::chrono::duration<double>(Clock::now().time_since_epoch()).count(); }
 
 constexpr size_t kMaxQueue = 1 << 20;
-constexpr int kMaxAhead = 3;          // ticks the loop may run ahead of the GPU
+constexpr int kMaxAhead = 3;          // dispatches the loop may run ahead of the GPU
+constexpr int kMaxTicks = 8;          // ticks one dispatch may enqueue while the active set stays fixed
 constexpr int kParamChunk = 6144;      // floats per parameter upload launch
 
 struct ParamChunk {
@@ -238,6 +242,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     d.mu = q.mu;
     d.dt = q.dt;
     d.zc = 16;
+    d.xyp = rsf::kDefaultXYPlanes;
     d.flip = (int)(s->tick & 1);  // its iteration k runs at tick (admission tick + k)
     // centring constants (the profiles are set below, exactly as rsf_evolve computes them)
     rsf::Fields f;
@@ -397,11 +402,29 @@ void loop(Server *s) {
             }
         }
         if (s->active.empty()) continue;
+        // Ticks to enqueue in this dispatch: the active set stays fixed until its first brick
+        // finishes, so up to that many ticks (at most kMaxTicks) go out without a host round
+        // trip -- unless a request waits in the queue (it may become admissible when a brick
+        // retires, and requests arriving meanwhile join after the dispatch) or a brick is to
+        // be cancelled or suspended (they leave after their current iteration).
+        int nticks = kMaxTicks;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (!s->queue.empty()) nticks = 1;
+        }
+        for (auto &r : s->active) {
+            nticks = std::min(nticks, r->req.iters - r->done_iters);
+            if (r->cancel.load() || r->suspend.load()) nticks = 1;
+        }
+        nticks = std::max(nticks, 1);
         // a tick counts only if the upload and every launch of it succeeded; otherwise the
         // requests of the active set fail with RSF_E_CUDA (queued ones are admitted later)
         bool ok = !s->groups_dirty || rebuild_groups(s);
-        for (const rsf::TiledGroup &g : s->groups)
-            if (ok && rsf::tiled_iterate(g, (int)(s->tick & 1), nullptr, s->s_comp) != cudaSuccess) ok = false;
+        for (int k = 0; k < nticks && ok; ++k) {
+            for (const rsf::TiledGroup &g : s->groups)
+                if (ok && rsf::tiled_iterate(g, (int)(s->tick & 1), nullptr, s->s_comp) != cudaSuccess) ok = false;
+            if (ok) ++s->tick;
+        }
         if (!ok) {
             cudaGetLastError();  // not sticky: later launches are not blamed for it
             for (auto &r : s->active) retire(s, r, RSF_E_CUDA);
@@ -410,12 +433,11 @@ void loop(Server *s) {
             s->groups_dirty = true;
             continue;
         }
-        ++s->tick;
         // retire finished or cancelled bricks
         std::vector<std::shared_ptr<Request>> keep;
         keep.reserve(s->active.size());
         for (auto &r : s->active) {
-            ++r->done_iters;
+            r->done_iters += nticks;
             const bool cancelled = r->cancel.load();
             const bool finished = r->done_iters >= r->req.iters;
             const bool suspended = !cancelled && !finished && r->suspend.load();

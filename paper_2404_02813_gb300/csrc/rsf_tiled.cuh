@@ -48,7 +48,8 @@ namespace tiled {
 
 constexpr int kXYT = 32;          // x/y kernel: output tile edge (x and y)
 constexpr int kXYThreads = 256;   // 8 warps
-constexpr int kXYPlanes = 16;      // z-planes per CTA of the x/y kernel
+// z-planes per CTA of the x/y kernel: BrickDev::xyp (tuned per brick group), kDefaultXYPlanes by default
+__host__ __device__ __forceinline__ int xy_planes(const BrickDev &B) { return B.xyp > 0 ? B.xyp : kDefaultXYPlanes; }
 constexpr int kZX = 32, kZY = 8;  // z march: columns per CTA
 constexpr int kZThreads = kZX * kZY;
 constexpr int kAZT = 64;          // x-z slab: output planes per CTA
@@ -350,13 +351,13 @@ struct VecLoaderH {  // NP = 1: (H I~, H); NP = 2: also ((1-H) I~, 1-H) (the Eq.
     }
 };
 
-// The x/y kernel body for one CTA of one brick: planes [za, za + kXYPlanes) of
+// The x/y kernel body for one CTA of one brick: planes [za, za + np) of
 // tile (x0, y0).  The global loads of plane z+1 are issued right after the
 // first barrier of plane z and land in registers while the convolutions run.
 // `Out` writes the NP pairs (pitch out.px).
 template <int R, int NP, class Loader, class Out>
 __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int ny, int nz, int x0, int y0, int za,
-                                        const TapPairs &t, float2 *sm) {
+                                        int np, const TapPairs &t, float2 *sm) {
     using L = XYLayout<R, NP>;
     constexpr int T = 2 * R + 1;
     constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
@@ -365,7 +366,7 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
     float2 *xc = sm + L::IN;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int zb_end = min(za + kXYPlanes, nz);
+    const int zb_end = min(za + np, nz);
     ld.fetch(za);
     for (int z = za; z < zb_end; ++z) {
         ld.store(in);
@@ -450,7 +451,7 @@ struct OutF4 {  // two x/y-convolved pairs interleaved per voxel (16 bytes), FP3
     }
 };
 
-// CTA -> (brick, tile) for the x/y kernels: tiles (tx, ty, tz) of 32 x 32 x kXYPlanes.
+// CTA -> (brick, tile) for the x/y kernels: tiles (tx, ty, tz) of 32 x 32 x xy_planes(B).
 struct XYTile {
     int b, x0, y0, za;
 };
@@ -458,7 +459,7 @@ __device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev 
     const int local = blockIdx.x - __ldg(G.starts + b);
     const int ntx = (B.nx + kXYT - 1) / kXYT, nty = (B.ny + kXYT - 1) / kXYT;
     const int tx = local % ntx, r = local / ntx;
-    return XYTile{b, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes};
+    return XYTile{b, tx * kXYT, (r % nty) * kXYT, (r / nty) * xy_planes(B)};
 }
 
 // NP = 1: (H I~, H) into B.u2 (Li's form); NP = 2: both sides of Eq. (10),
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <=
         if (B.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(img) % (4 * sizeof(ImgT)) == 0) {
             VecLoaderH<R, ImgT, NP> ld(q, img, inv_s, nms, B.nx, B.ny, tl.x0, tl.y0);
-            xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
+            xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
             return;
         }
     }
@@ -494,7 +495,7 @@ __global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <=
     pro.inv_s = inv_s;
     pro.nms = nms;
     ScalarLoader<R, NP, Pro> ld(pro, B.nx, B.ny, B.nx, tl.x0, tl.y0);
-    xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
+    xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
 }
 
 template <int R, class S>
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(kXYThreads, 3) k_tb_xy(GroupArgs G, TapPairs t
     ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
     ScalarLoader<R, 1, ProAB<S>> ld(pro, B.nx, B.ny, B.px, tl.x0, tl.y0);
-    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, t, sm);
+    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
 }
 
 // ------------------------------------------------------------------ A: z
@@ -622,23 +623,24 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
         const BrickDev &B = G.bricks[id.b];
         const int x = id.x0 + lane;
         const int zb = warp * kAZO;
-        if (x < B.nx) {
+        const int bnx = B.nx, bny = B.ny, bnz = B.nz;  // read once: the stores below might alias B
+        if (x < bnx) {
             const float l1 = B.lambda1, l2 = B.lambda2;
             float2 w[WIN];
 #pragma unroll
             for (int j = 0; j < WIN; ++j) w[j] = buf[(zb + j) * 32 + lane];
-            const long long pplane = (long long)B.px * B.ny;
+            const long long pplane = (long long)B.px * bny;
             const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
             V2 *ab = reinterpret_cast<V2 *>(B.ab) + off;
             const float *ki = reinterpret_cast<const float *>(buf + ROWS * 32) + zb * 32 + lane;
-            const float kxy = __ldg(B.prof + x) * __ldg(B.prof + B.nx + id.y);
+            const float kxy = __ldg(B.prof + x) * __ldg(B.prof + bnx + id.y);
             float2 res = make_float2(0.f, 0.f);  // rounding residual carried along z (16-bit storage)
-            const float *pz = B.prof + B.nx + B.ny + id.z0 + zb;
+            const float *pz = B.prof + bnx + bny + id.z0 + zb;
             float *const dump = B.dump;
 #pragma unroll
             for (int o = 0; o < kAZO; ++o) {
                 const int zo = id.z0 + zb + o;
-                if (zo < B.nz) {
+                if (zo < bnz) {
                     float2 acc = make_float2(0.f, 0.f);  // (K*(H I~), K*H)
 #pragma unroll
                     for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
@@ -650,7 +652,7 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
                     const float f2 = den > 0x1p-20f * k1 ? __fdividef(ki[o * 32] - acc.x, den) : f1;
                     const float2 v = make_float2(l1 * f1 - l2 * f2, l1 * (f1 * f1) - l2 * (f2 * f2));
                     if constexpr (std::is_same<S, float>::value) {
-                        ab[o * pplane] = v;
+                        *ab = v;
                     } else {
                         // 16-bit storage: the rounding residual of each plane is carried into the
                         // next plane of the column before it is rounded (first-order noise
@@ -660,8 +662,9 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
                         const V2 st = Store<S>::pack2(want);
                         const float2 got = Store<S>::unpack2(st);
                         res = make_float2(want.x - got.x, want.y - got.y);
-                        ab[o * pplane] = st;
+                        *ab = st;
                     }
+                    ab += pplane;
                     if (dump) {
                         const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
                         const long long n = (long long)B.nx * B.ny * B.nz;
@@ -752,13 +755,15 @@ __global__ void __launch_bounds__(kAZThreads, 2) k_ta_z4(GroupArgs G, TapPairs t
             const long long pplane = (long long)B.px * B.ny;
             const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
             float2 *fits = B.abxy + off;
+            const int bnz = B.nz;
             float *const dump = B.dump;
 #pragma unroll
             for (int o = 0; o < kAZO; ++o) {
                 const int zo = id.z0 + zb + o;
-                if (zo < B.nz) {
+                if (zo < bnz) {
                     const float f1 = __fdividef(acc[0][o].x, acc[0][o].y), f2 = __fdividef(acc[1][o].x, acc[1][o].y);
-                    fits[o * pplane] = make_float2(f1, f2);
+                    *fits = make_float2(f1, f2);
+                    fits += pplane;
                     if (dump) {
                         const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
                         const long long n = (long long)B.nx * B.ny * B.nz;
@@ -786,7 +791,7 @@ __global__ void __launch_bounds__(kXYThreads) k_ki_xy(BrickDev B, TapPairs t) {
     ProI<ImgT> pro{reinterpret_cast<const ImgT *>(B.img), B.cs[1], -B.cs[0] * B.cs[1]};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
     ScalarLoader<R, 1, ProI<ImgT>> ld(pro, B.nx, B.ny, B.nx, tx * kXYT, (r % nty) * kXYT);
-    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tx * kXYT, (r % nty) * kXYT, (r / nty) * kXYPlanes, t, sm);
+    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tx * kXYT, (r % nty) * kXYT, (r / nty) * xy_planes(B), xy_planes(B), t, sm);
 }
 
 template <int R>

@@ -124,7 +124,7 @@ cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaS
 
 void tiled_cta_counts(const BrickDev &b, unsigned counts[4]) {
     const unsigned ntx = (b.nx + tiled::kXYT - 1) / tiled::kXYT, nty = (b.ny + tiled::kXYT - 1) / tiled::kXYT;
-    const unsigned nzp = (b.nz + tiled::kXYPlanes - 1) / tiled::kXYPlanes;
+    const unsigned nzp = (b.nz + tiled::xy_planes(b) - 1) / tiled::xy_planes(b);
     counts[0] = ntx * nty * nzp;
     counts[1] = (unsigned)((b.nz + tiled::kAZT - 1) / tiled::kAZT) * ((b.nx + 31) / 32) * b.ny;
     counts[2] = counts[0];

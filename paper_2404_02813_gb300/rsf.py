@@ -28,7 +28,7 @@ EXPORTED = ("rsf_create", "rsf_destroy", "rsf_stream", "rsf_evolve", "rsf_step_s
             "rsf_prof_count", "rsf_prof_name", "rsf_prof_get", "rsf_last_error", "rsf_evolve_noalloc",
             "rsf_set_option", "rsf_evolve_batch", "rsf_submit", "rsf_poll", "rsf_wait", "rsf_cancel",
             "rsf_serve_stats", "rsf_evolve_curtain", "rsf_init_phi0", "rsf_overlap", "rsf_isosurface",
-            "rsf_suspend")
+            "rsf_suspend", "rsf_autotune_report")
 
 OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION, OPT_SERVE_SLOTS = 1, 2, 3, 4, 5, 6, 7
 OPT_FORCE = 8
@@ -102,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     L.rsf_prof_get.restype = i32
     L.rsf_evolve_noalloc.argtypes = [vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, vp]
     L.rsf_evolve_noalloc.restype = i32
+    L.rsf_autotune_report.argtypes = [vp, ctypes.c_char_p, i32]
+    L.rsf_autotune_report.restype = i32
     L.rsf_evolve_batch.argtypes = [vp, ctypes.POINTER(Brick), i32]
     L.rsf_evolve_batch.restype = i32
     L.rsf_evolve_curtain.argtypes = [vp, vp, i32, i64, i64, i64, vp, vp, f32, f32, f32, f32, f32, f32, f32, i32, i32, i32]
@@ -410,6 +412,20 @@ class Context:
         self.set_option(OPT_FORCE, FORCES[name])
 
     # kernel timing ---------------------------------------------------------
+    def autotune_report(self):
+        """rsf_autotune_report parsed: one dict per tuned brick group."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(load_library().rsf_autotune_report(self._h, buf, len(buf)))
+        out = []
+        for line in buf.value.decode().splitlines():
+            key, *fields = line.split()
+            d = {"group": key}
+            for f in fields:
+                k, v = f.split("=", 1)
+                d[k] = v if k == "order" else (float(v) if "ms" in k else int(v))
+            out.append(d)
+        return out
+
     def prof_enable(self, on: bool = True):
         _check(load_library().rsf_prof_enable(self._h, 1 if on else 0))
 

@@ -86,3 +86,23 @@ def test_batch_rejects_bad_brick(bricks):
                           (torch.from_numpy(v).cuda(), torch.from_numpy(p0).cuda(), bad, it)])
     assert e.value.status == -1 and "brick 1" in str(e.value)
     ctx.close()
+
+
+def test_autotune_report_lists_each_group(bricks):
+    """With RSF_OPT_AUTOTUNE the batch picks, per brick group, the x/y planes per CTA,
+    the update kernel's z chunk and the brick order by timing; the report lists one
+    entry per group with a choice from the candidate sets and a time no worse than the
+    defaults' (the defaults are the first candidate).  The results stay bit-identical
+    to rsf_evolve (test_batch_equals_plain_bitwise)."""
+    ctx = rsf.Context(0)
+    assert ctx.autotune_report() == []
+    ctx.set_option(rsf.OPT_AUTOTUNE, 1)
+    items = [(torch.from_numpy(v).cuda(), torch.from_numpy(p0).cuda(), p, it) for v, p0, p, it in bricks]
+    ctx.evolve_batch(items)
+    rep = ctx.autotune_report()
+    groups = {(int(2 * p["sigma"] + 0.5), np.dtype(v.dtype).name) for v, _, p, it in bricks if it > 0}
+    assert len(rep) == len(groups), rep
+    for r in rep:
+        assert r["xyp"] in (8, 16, 32) and r["zc"] >= 16 and r["order"] in ("largest", "smallest")
+        assert 0 < r["ms"] <= r["default_ms"]
+    ctx.close()
