@@ -363,9 +363,11 @@ rsf_status rsf_autotune_report(rsf_ctx *ctx, char *buf, int32_t cap);
  * first poll that returns a final status (later polls: RSF_E_NOTFOUND).
  * rsf_wait blocks up to timeout_ms (< 0: no limit) for a final status, then
  * behaves as rsf_poll; on expiry it returns RSF_E_TIMEOUT and keeps the ticket.
- * The loop advances its active bricks by dispatches of one to eight
- * iterations: while no brick is due to finish and nothing waits in the queue,
- * a dispatch enqueues several iterations without a host round trip.
+ * Active requests are advanced in four lanes by voxel count (below 2^19, 2^21,
+ * 2^23 voxels, and larger), each on its own stream; within a lane every brick
+ * advances one iteration per tick, in dispatches of one to eight ticks: while
+ * no brick of the lane is due to finish and nothing waits in the queue, a
+ * dispatch enqueues several ticks without a host round trip.
  * rsf_cancel marks a request cancelled: it leaves the queue, or the batch at
  * the end of the current dispatch, and its phi_out is not written.
  * rsf_suspend marks a request for suspension (checkpointing): it leaves the

@@ -2,23 +2,26 @@
 // rsf_cancel: continuous batching of brick segmentation requests at iteration
 // granularity.
 //
-// A scheduler thread per context runs "ticks".  Before each tick it admits
+// A scheduler thread per context runs "ticks".  Before each round it admits
 // queued requests in arrival order while their device footprint fits the
-// context's HBM budget: the brick's fields are allocated from the stream-
-// ordered pool, its image statistics, K*1 profiles, phi0 and q are prepared on
-// a set-up stream, and the compute stream waits on that work.  A tick is one
-// iteration of every active brick -- one launch per kernel for each group of
-// bricks sharing a kernel radius, image type, storage and force form (the batched kernels
-// of rsf_evolve_batch); a brick admitted at tick T0 runs its iteration k at
-// tick T0 + k (its buffer parity is flipped accordingly).  A brick that has
-// done its iterations (or was cancelled, or suspended after its current
-// iteration) retires at once: its phi is copied to
-// the caller's phi_out, a host callback stamps its completion time, and its
+// context's HBM budget and a slot is free: the brick's fields are allocated
+// from the stream-ordered pool, its image statistics, K*1 profiles, phi0 and q
+// are prepared on a set-up stream, and the compute stream of its lane waits on
+// that work.  Active bricks are split into four lanes by voxel count, each with
+// its own stream: a tick of a lane is one iteration of every brick in it -- one
+// launch per kernel for each group of bricks sharing a kernel radius, image
+// type, storage and force form (the batched kernels of rsf_evolve_batch); a
+// brick admitted at its lane's tick T0 runs its iteration k at tick T0 + k (its
+// buffer parity is flipped accordingly).  Lanes advance independently, so a
+// small brick is not paced by the iterations of large ones, and their kernels
+// overlap on the GPU.  A brick that has done its iterations (or was cancelled,
+// or suspended after its current iteration) retires at once: its phi is copied
+// to the caller's phi_out, a host callback stamps its completion time, and its
 // memory returns to the pool in stream order, so the next admission can use
-// it.  While the active set cannot change (no brick is due to finish, nothing
-// waits in the queue, nothing is to be cancelled or suspended), one dispatch
-// enqueues up to kMaxTicks ticks without a host round trip; the loop runs at
-// most kMaxAhead dispatches ahead of the GPU.
+// it.  While a lane's active set cannot change (no brick due to finish,
+// nothing waiting in the queue, nothing to cancel or suspend), one dispatch
+// enqueues up to kMaxTicks of its ticks without a host round trip; each lane
+// runs at most kMaxAhead dispatches ahead of the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -46,6 +49,7 @@ double now_s() { return std::chrono::duration<double>(Clock::now().time_since_ep
 constexpr size_t kMaxQueue = 1 << 20;
 constexpr int kMaxAhead = 3;          // dispatches the loop may run ahead of the GPU
 constexpr int kMaxTicks = 8;          // ticks one dispatch may enqueue while the active set stays fixed
+constexpr int kLanes = 4;             // per-iteration cost classes, each advanced on its own stream
 constexpr int kParamChunk = 6144;      // floats per parameter upload launch
 
 struct ParamChunk {
@@ -77,8 +81,25 @@ struct Request {
     size_t bytes = 0;
     void *mem = nullptr;
     int done_iters = 0;
+    int lane = 0;
     cudaEvent_t ready = nullptr;
 };
+
+// Active bricks of one cost class: advanced together, one tick (iteration) at a
+// time, on the lane's stream; lanes progress independently of each other, so a
+// small brick is not paced by the iterations of large ones.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    std::vector<std::shared_ptr<Request>> active;
+    uint64_t tick = 0;
+    bool groups_dirty = true;
+    std::vector<rsf::TiledGroup> groups;
+    DescBuffers desc;
+    std::deque<cudaEvent_t> inflight;  // one event per dispatch not yet known complete
+};
+
+// The lane of a brick by its voxel count: below 2^19, 2^21, 2^23, and larger.
+int lane_of(long long n) { return n < (1LL << 19) ? 0 : (n < (1LL << 21) ? 1 : (n < (1LL << 23) ? 2 : 3)); }
 
 struct Server;
 
@@ -99,14 +120,9 @@ struct Server {
     uint64_t next_ticket = 1;
     bool stop = false;
     // scheduler-thread state
-    std::vector<std::shared_ptr<Request>> active;
-    cudaStream_t s_comp = nullptr, s_setup = nullptr;
+    Lane lanes[kLanes];
+    cudaStream_t s_setup = nullptr;
     float *partials = nullptr;
-    uint64_t tick = 0;
-    std::deque<cudaEvent_t> inflight;
-    bool groups_dirty = true;
-    std::vector<rsf::TiledGroup> groups;
-    DescBuffers desc;
     int sms = 0;
     // statistics (mu)
     uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, suspended = 0, admitted = 0;
@@ -204,6 +220,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     const long long n = (long long)q.nx * q.ny * q.nz;
     const int px = rsf::tiled_pitch((int)q.nx);
     r->n = n;
+    r->lane = lane_of(n);
     r->taps = make_taps(q.sigma);
     r->imgtype = (int)q.vt;
     r->storage = (int)q.storage;
@@ -243,7 +260,7 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
     d.dt = q.dt;
     d.zc = 16;
     d.xyp = rsf::kDefaultXYPlanes;
-    d.flip = (int)(s->tick & 1);  // its iteration k runs at tick (admission tick + k)
+    d.flip = (int)(s->lanes[r->lane].tick & 1);  // its iteration k runs at its lane's tick (admission + k)
     // centring constants (the profiles are set below, exactly as rsf_evolve computes them)
     rsf::Fields f;
     f.d = rsf::Dims{d.nx, d.ny, d.nz, (long long)q.nx * q.ny, n};
@@ -285,12 +302,13 @@ bool admit(Server *s, const std::shared_ptr<Request> &r) {
 // stream order.
 void retire(Server *s, const std::shared_ptr<Request> &r, int outcome) {
     rsf_ctx *c = s->ctx;
+    const cudaStream_t st_lane = s->lanes[r->lane].stream;
     int st = outcome;
     if ((st == RSF_OK || st == RSF_SUSPENDED) &&
-        xfer(r->req.phi_out, r->d.phi[r->done_iters & 1], sizeof(float) * r->n, s->s_comp) != cudaSuccess)
+        xfer(r->req.phi_out, r->d.phi[r->done_iters & 1], sizeof(float) * r->n, st_lane) != cudaSuccess)
         st = RSF_E_CUDA;
-    cudaLaunchHostFunc(s->s_comp, done_cb, new DoneArg{s, r, st});
-    cudaFreeAsync(r->mem, s->s_comp);
+    cudaLaunchHostFunc(st_lane, done_cb, new DoneArg{s, r, st});
+    cudaFreeAsync(r->mem, st_lane);
     if (r->ready) cudaEventDestroy(r->ready);
     r->mem = nullptr;
     std::lock_guard<std::mutex> lk(c->alloc_mu);
@@ -299,8 +317,8 @@ void retire(Server *s, const std::shared_ptr<Request> &r, int outcome) {
 
 // Launch groups of the active set; false (and the groups left empty) when the
 // descriptor upload failed.
-bool rebuild_groups(Server *s) {
-    std::vector<std::shared_ptr<Request>> order = s->active;
+bool rebuild_groups(Server *s, Lane &L) {
+    std::vector<std::shared_ptr<Request>> order = L.active;
     std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a->n > b->n; });
     std::vector<GroupSpec> specs;
     std::vector<std::tuple<int, int, int, int>> keys;
@@ -329,20 +347,78 @@ bool rebuild_groups(Server *s) {
     }
     // the copy comes from pageable memory and waits for the compute stream; the
     // loop already bounds how far it runs ahead, so this costs one short sync
-    s->groups.clear();
+    L.groups.clear();
     rsf_status st;
     if (s->inject_upload > 0 && (int64_t)++s->uploads == s->inject_upload) {
         rsf::set_last_error("injected descriptor upload failure");
         st = RSF_E_CUDA;
     } else {
-        st = upload_groups(s->ctx, s->desc, s->s_comp, specs, &s->groups);
+        st = upload_groups(s->ctx, L.desc, L.stream, specs, &L.groups);
     }
     if (st != RSF_OK) {
-        s->groups.clear();
+        L.groups.clear();
         return false;
     }
-    s->groups_dirty = false;
+    L.groups_dirty = false;
     return true;
+}
+
+// One dispatch of a lane: up to kMaxTicks ticks, then the retirements they cause.
+void dispatch(Server *s, Lane &L, bool queued) {
+    // Ticks to enqueue in this dispatch: the lane's active set stays fixed until its first
+    // brick finishes, so up to that many ticks (at most kMaxTicks) go out without a host
+    // round trip -- unless a request waits in the queue (it may become admissible when a
+    // brick retires, and requests arriving meanwhile join after the dispatch) or a brick is
+    // to be cancelled or suspended (they leave after their current iteration).
+    int nticks = queued ? 1 : kMaxTicks;
+    for (auto &r : L.active) {
+        nticks = std::min(nticks, r->req.iters - r->done_iters);
+        if (r->cancel.load() || r->suspend.load()) nticks = 1;
+    }
+    nticks = std::max(nticks, 1);
+    // a tick counts only if the upload and every launch of it succeeded; otherwise the
+    // lane's requests fail with RSF_E_CUDA (queued ones are admitted later)
+    bool ok = !L.groups_dirty || rebuild_groups(s, L);
+    for (int k = 0; k < nticks && ok; ++k) {
+        for (const rsf::TiledGroup &g : L.groups)
+            if (ok && rsf::tiled_iterate(g, (int)(L.tick & 1), nullptr, L.stream) != cudaSuccess) ok = false;
+        if (ok) ++L.tick;
+    }
+    if (!ok) {
+        cudaGetLastError();  // not sticky: later launches are not blamed for it
+        for (auto &r : L.active) retire(s, r, RSF_E_CUDA);
+        L.active.clear();
+        L.groups.clear();
+        L.groups_dirty = true;
+        return;
+    }
+    // retire finished or cancelled bricks
+    std::vector<std::shared_ptr<Request>> keep;
+    keep.reserve(L.active.size());
+    for (auto &r : L.active) {
+        r->done_iters += nticks;
+        const bool cancelled = r->cancel.load();
+        const bool finished = r->done_iters >= r->req.iters;
+        const bool suspended = !cancelled && !finished && r->suspend.load();
+        if (cancelled || finished || suspended) {
+            retire(s, r, cancelled ? RSF_E_CANCELLED : (suspended ? RSF_SUSPENDED : RSF_OK));
+            L.groups_dirty = true;
+        } else {
+            keep.push_back(r);
+        }
+    }
+    L.active.swap(keep);
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(ev, L.stream);
+        L.inflight.push_back(ev);
+    }
+}
+
+size_t n_active(const Server *s) {
+    size_t k = 0;
+    for (const Lane &L : s->lanes) k += L.active.size();
+    return k;
 }
 
 void loop(Server *s) {
@@ -352,7 +428,7 @@ void loop(Server *s) {
         std::vector<std::shared_ptr<Request>> admit_now;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || !s->active.empty(); });
+            s->cv.wait(lk, [&] { return s->stop || !s->queue.empty() || n_active(s) > 0; });
             if (s->stop) break;
             // FIFO admission by footprint
             while (!s->queue.empty()) {
@@ -382,8 +458,8 @@ void loop(Server *s) {
                     used = c->used;
                     budget = c->budget;
                 }
-                if (used + need > budget && !s->active.empty()) break;  // wait for retirements
-                if ((int64_t)(s->active.size() + admit_now.size()) >= s->slots) break;  // wait for a free slot
+                if (used + need > budget && n_active(s) > 0) break;  // wait for retirements
+                if ((int64_t)(n_active(s) + admit_now.size()) >= s->slots) break;  // wait for a free slot
                 s->queue.pop_front();
                 admit_now.push_back(r);
                 if (used + need > budget) break;  // nothing active: admit it alone and try
@@ -391,74 +467,45 @@ void loop(Server *s) {
         }
         for (auto &r : admit_now) {
             if (admit(s, r)) {
-                cudaStreamWaitEvent(s->s_comp, r->ready, 0);
+                Lane &L = s->lanes[r->lane];
+                cudaStreamWaitEvent(L.stream, r->ready, 0);
                 r->done_iters = 0;
                 if (r->req.iters == 0) {
                     retire(s, r, RSF_OK);
                 } else {
-                    s->active.push_back(r);
-                    s->groups_dirty = true;
+                    L.active.push_back(r);
+                    L.groups_dirty = true;
                 }
             }
         }
-        if (s->active.empty()) continue;
-        // Ticks to enqueue in this dispatch: the active set stays fixed until its first brick
-        // finishes, so up to that many ticks (at most kMaxTicks) go out without a host round
-        // trip -- unless a request waits in the queue (it may become admissible when a brick
-        // retires, and requests arriving meanwhile join after the dispatch) or a brick is to
-        // be cancelled or suspended (they leave after their current iteration).
-        int nticks = kMaxTicks;
+        bool queued;
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            if (!s->queue.empty()) nticks = 1;
+            queued = !s->queue.empty();
         }
-        for (auto &r : s->active) {
-            nticks = std::min(nticks, r->req.iters - r->done_iters);
-            if (r->cancel.load() || r->suspend.load()) nticks = 1;
-        }
-        nticks = std::max(nticks, 1);
-        // a tick counts only if the upload and every launch of it succeeded; otherwise the
-        // requests of the active set fail with RSF_E_CUDA (queued ones are admitted later)
-        bool ok = !s->groups_dirty || rebuild_groups(s);
-        for (int k = 0; k < nticks && ok; ++k) {
-            for (const rsf::TiledGroup &g : s->groups)
-                if (ok && rsf::tiled_iterate(g, (int)(s->tick & 1), nullptr, s->s_comp) != cudaSuccess) ok = false;
-            if (ok) ++s->tick;
-        }
-        if (!ok) {
-            cudaGetLastError();  // not sticky: later launches are not blamed for it
-            for (auto &r : s->active) retire(s, r, RSF_E_CUDA);
-            s->active.clear();
-            s->groups.clear();
-            s->groups_dirty = true;
-            continue;
-        }
-        // retire finished or cancelled bricks
-        std::vector<std::shared_ptr<Request>> keep;
-        keep.reserve(s->active.size());
-        for (auto &r : s->active) {
-            r->done_iters += nticks;
-            const bool cancelled = r->cancel.load();
-            const bool finished = r->done_iters >= r->req.iters;
-            const bool suspended = !cancelled && !finished && r->suspend.load();
-            if (cancelled || finished || suspended) {
-                retire(s, r, cancelled ? RSF_E_CANCELLED : (suspended ? RSF_SUSPENDED : RSF_OK));
-                s->groups_dirty = true;
-            } else {
-                keep.push_back(r);
+        // each lane with work and fewer than kMaxAhead dispatches in flight gets one dispatch
+        bool dispatched = false;
+        for (Lane &L : s->lanes) {
+            if (L.active.empty()) continue;
+            while (!L.inflight.empty()) {
+                const cudaError_t q = cudaEventQuery(L.inflight.front());
+                if (q == cudaErrorNotReady) {
+                    if (cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+                    break;
+                }
+                cudaEventDestroy(L.inflight.front());
+                L.inflight.pop_front();
             }
+            if ((int)L.inflight.size() >= kMaxAhead) continue;
+            dispatch(s, L, queued);
+            dispatched = true;
         }
-        s->active.swap(keep);
-        // bound the run-ahead
-        cudaEvent_t ev;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) {
-            cudaEventRecord(ev, s->s_comp);
-            s->inflight.push_back(ev);
-        }
-        while ((int)s->inflight.size() > kMaxAhead) {
-            cudaEventSynchronize(s->inflight.front());
-            cudaEventDestroy(s->inflight.front());
-            s->inflight.pop_front();
+        if (!dispatched) {  // every lane with work is kMaxAhead dispatches ahead of the GPU
+            for (Lane &L : s->lanes)
+                if (!L.inflight.empty()) {
+                    cudaEventSynchronize(L.inflight.front());
+                    break;
+                }
         }
     }
     // shutdown: cancel what is queued or active, let the GPU finish
@@ -469,12 +516,16 @@ void loop(Server *s) {
         s->queue.clear();
     }
     for (auto &r : rest) finish_now(s, r, RSF_E_CANCELLED);
-    for (auto &r : s->active) retire(s, r, RSF_E_CANCELLED);
-    s->active.clear();
-    cudaStreamSynchronize(s->s_comp);
+    for (Lane &L : s->lanes) {
+        for (auto &r : L.active) retire(s, r, RSF_E_CANCELLED);
+        L.active.clear();
+    }
+    for (Lane &L : s->lanes) cudaStreamSynchronize(L.stream);
     cudaStreamSynchronize(s->s_setup);
-    for (cudaEvent_t e : s->inflight) cudaEventDestroy(e);
-    s->inflight.clear();
+    for (Lane &L : s->lanes) {
+        for (cudaEvent_t e : L.inflight) cudaEventDestroy(e);
+        L.inflight.clear();
+    }
 }
 
 Server *server(rsf_ctx *c, rsf_status *st) {
@@ -484,8 +535,9 @@ Server *server(rsf_ctx *c, rsf_status *st) {
     s->ctx = c;
     cudaSetDevice(c->device);
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, c->device);
-    if (cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->s_setup, cudaStreamNonBlocking) != cudaSuccess) {
+    bool streams_ok = cudaStreamCreateWithFlags(&s->s_setup, cudaStreamNonBlocking) == cudaSuccess;
+    for (Lane &L : s->lanes) streams_ok = streams_ok && cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!streams_ok) {
         *st = cuda_fail(cudaGetLastError(), "serving streams");
         delete s;
         return nullptr;
@@ -515,8 +567,10 @@ void rsf_serve_shutdown(rsf_ctx *c) {
     s->cv.notify_all();
     if (s->th.joinable()) s->th.join();
     dev_free(c, s->partials, sizeof(float) * 3 * rsf::kStatBlocks);
-    free_desc(c, s->desc);
-    cudaStreamDestroy(s->s_comp);
+    for (Lane &L : s->lanes) {
+        free_desc(c, L.desc);
+        cudaStreamDestroy(L.stream);
+    }
     cudaStreamDestroy(s->s_setup);
     delete s;
     c->server = nullptr;
