@@ -374,7 +374,15 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
         if (z + 1 < zb_end) ld.fetch(z + 1);
         {
             const int h = lane >> 4, r = (lane >> 2) & 3, g = lane & 3;
-            for (int item = warp; item < NP * NRB * 2; item += kXYThreads / 32) {
+            // items (8 rows x 16 columns of one pair) dealt to the warps round-robin; at radius
+            // <= 6 and for two pairs a warp's items warp + 8 i run in a compile-time number of
+            // rounds (measured faster there; slower at radius 8 with one pair)
+            constexpr int NITEMS = NP * NRB * 2, NW8 = kXYThreads / 32;
+            constexpr bool STATIC = R <= 6 || NP == 2;
+            constexpr int NROUNDS = STATIC ? (NITEMS + NW8 - 1) / NW8 : 1;
+#pragma unroll
+            for (int i = 0; i < NROUNDS; ++i)
+            for (int item = warp + NW8 * i; item < NITEMS; item += STATIC ? NITEMS : NW8) {
                 const int p = item / (NRB * 2);
                 const int rem = item - p * NRB * 2;
                 const int row = (rem >> 1) * 8 + h * 4 + r;
