@@ -61,20 +61,21 @@ PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
+NCU_SHA = "45925106e2b05782"
 NCU_TRAFFIC = {
-    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "f795d4d6476f93ce",
+    k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": NCU_SHA,
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
-    for k, v in {"rsf_ta_xy": 13.29, "rsf_ta_z": 19.34, "rsf_tb_xy": 15.28, "rsf_tb_z": 21.94}.items()
+    for k, v in {"rsf_ta_xy": 13.21, "rsf_ta_z": 19.35, "rsf_tb_xy": 15.28, "rsf_tb_z": 21.97}.items()
 }
 
-# Issue slots per voxel measured by ncu (smsp__inst_executed.sum * 32 / voxels: warp
-# instructions, counted per thread lane), same capture conditions and gating as
-# NCU_TRAFFIC.  The kernels are issue-bound; against one warp instruction per
-# cycle per SM sub-partition (4 per SM) this gives the issue roofline.
+# Warp instructions issued per voxel measured by ncu (smsp__inst_executed.sum / voxels),
+# same capture conditions and gating as NCU_TRAFFIC.  The kernels are issue-bound;
+# against one warp instruction per cycle per SM sub-partition (4 per SM) this gives
+# the issue roofline.
 NCU_INST = {
-    k: {"inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": "f795d4d6476f93ce",
+    k: {"warp_inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": NCU_SHA,
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage"}
-    for k, v in {"rsf_ta_xy": 121.9, "rsf_ta_z": 123.1, "rsf_tb_xy": 96.0, "rsf_tb_z": 245.5}.items()
+    for k, v in {"rsf_ta_xy": 3.67, "rsf_ta_z": 3.55, "rsf_tb_xy": 2.95, "rsf_tb_z": 6.58}.items()
 }
 SM_SUBPARTITIONS = 4  # warp schedulers per SM, one warp instruction issued per cycle each
 
@@ -750,6 +751,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=None, help="cube edge instead of the workload's (profiling runs)")
     ap.add_argument("--iters", type=int, default=None, help="iterations per step instead of the workload's")
+    ap.add_argument("--sigma", type=float, default=None, help="kernel sigma instead of the workload's (profiling runs)")
     ap.add_argument("--path", default="auto", choices=["auto", "passes", "tiled"])
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
@@ -784,6 +786,8 @@ def main():
             dist.barrier()
 
     vol, phi0, params, iters = make_workload(args.workload, rank, args.size, args.iters)
+    if args.sigma is not None:
+        params = dict(params, sigma=args.sigma)
     n_vox = vol.size
     v = torch.from_numpy(vol).cuda()
     ph0 = torch.from_numpy(phi0).cuda()
@@ -938,9 +942,9 @@ def main():
         if ti and same_case and ti.get("source_sha") == _source_sha(ti.get("source", "")):
             sms = torch.cuda.get_device_properties(local).multi_processor_count
             mhz = clk.get("sm_mhz") or clk.get("sm_max_mhz") or 2070.0
-            ach = ti["inst_per_voxel"] / 32.0 * n_vox / avg_s
+            ach = ti["warp_inst_per_voxel"] * n_vox / avg_s
             pk = sms * SM_SUBPARTITIONS * mhz * 1e6
-            issue = {"kernel": dom, "warp_inst_per_voxel": ti["inst_per_voxel"] / 32.0,
+            issue = {"kernel": dom, "warp_inst_per_voxel": ti["warp_inst_per_voxel"],
                      "achieved_warp_inst_s": ach, "peak_warp_inst_s": pk, "frac": ach / pk, "sm_mhz": mhz,
                      "note": "instruction issue roofline of the dominant kernel: ncu-counted warp instructions "
                              "per voxel x voxels / CUDA-event launch time, against one issue per cycle per SM "
