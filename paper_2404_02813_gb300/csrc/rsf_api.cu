@@ -157,6 +157,8 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
         g.taps = gs.taps;
         g.bricks = buf.d_bricks + all.size();
         g.nb = nb;
+        g.dump = 0;
+        for (const rsf::BrickDev &b : gs.bricks) g.dump |= b.dump != nullptr;
         const size_t s0 = starts.size();
         starts.resize(s0 + 4 * (size_t)(nb + 1));
         unsigned long long tot[4] = {0, 0, 0, 0};

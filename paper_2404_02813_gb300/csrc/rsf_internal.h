@@ -118,6 +118,7 @@ struct TiledGroup {
     int nb;
     const int *starts[4];   // device: per kernel, nb + 1 CTA offsets
     unsigned ncta[4];       // CTAs per kernel launch
+    int dump;               // 1: some brick has a stage dump (its update kernel writes g, kappa, L)
 };
 
 constexpr int kDefaultXYPlanes = 16;

@@ -921,7 +921,9 @@ constexpr size_t tbz_smem() {
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-template <int R, class ImgT>
+// DUMP: also write g, kappa and L of every output to B.dump (rsf_step_stages); a
+// separate instantiation keeps the iteration's kernel free of it.
+template <int R, class ImgT, bool DUMP = false>
 __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(GroupArgs G, TapPairs t) {
     constexpr bool DEEP = tbz_deep<R>();
     constexpr bool PHI_ASYNC = DEEP;  // phi planes copied into the ring two steps ahead (cp.async)
@@ -1077,14 +1079,17 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
     // take no convolution and K*1 is 1
     const float pxy = R == 0 ? 1.f : (active ? __ldg(B.prof + x) * __ldg(B.prof + nx + y) : 0.f);
     const float *profz = B.prof + nx + ny + z0;
-    const float l1 = B.lambda1, l2 = B.lambda2, l12 = l1 - l2, s2 = B.cs[2];
+    const float l1 = B.lambda1, l2 = B.lambda2, s2 = B.cs[2];
+    // the data term's constants folded: s^2 (l1 - l2) p_x p_y (times p_z per plane), -2 s^2, and
+    // for the Eq. (15) form s^2 l1, s^2 l2
+    const float cK = s2 * (l1 - l2) * pxy, m2s2 = -2.f * s2, s2l1 = s2 * l1, s2l2 = s2 * l2;
     const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
-    const float eps = B.eps, eps_pi = eps * INV_PI, eps2 = eps * eps;
-    const float mu = B.mu, nu = B.nu, dt = B.dt;
+    const float eps = B.eps, eps2 = eps * eps;
+    const float nu = B.nu, dt_mu = B.dt * B.mu, dt_eps_pi = B.dt * (eps * INV_PI);
     const ImgT *img = reinterpret_cast<const ImgT *>(B.img) + colp;
     float *phi_out = (par ? B.phi[0] : B.phi[1]) + colp;
     float *q_out = (par ? B.q[0] : B.q[1]) + colp;
-    float *const dump = B.dump;
+    float *const dump = DUMP ? B.dump : nullptr;
     const long long n = (long long)plane * nz;
     // the centred image and p_z at output plane r (unused values past the chunk: 0 and 1)
     auto img_at = [&](int r) -> float {
@@ -1204,12 +1209,11 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
                     float2 g;
                     if constexpr (R == 0) {  // Eq. (15), sigma_2 = 0: the ring holds (f1, f2)
                         const float2 d1 = f2sub(im, make_float2(a0.x, a1.x)), d2 = f2sub(im, make_float2(a0.y, a1.y));
-                        g = f2mul(f2v(s2), __ffma2_rn(f2v(l1), f2mul(d1, d1), f2mul(f2v(-l2), f2mul(d2, d2))));
-                    } else {  // Li's data terms from K*a, K*b
-                        const float2 K1 = f2mul(f2v(pxy), make_float2(pz0, pz1));
-                        const float2 t1 = f2mul(f2mul(f2v(l12), K1), f2mul(im, im));
-                        const float2 t2 = __ffma2_rn(f2mul(f2v(-2.f), im), make_float2(a0.x, a1.x), t1);
-                        g = f2mul(f2v(s2), f2add(t2, make_float2(a0.y, a1.y)));
+                        g = __ffma2_rn(f2v(s2l1), f2mul(d1, d1), f2mul(f2v(-s2l2), f2mul(d2, d2)));
+                    } else {  // Li's data terms from K*a, K*b: s^2 [(l1 - l2) K1 I~^2 - 2 I~ K*a + K*b]
+                        const float2 t1 = f2mul(f2mul(f2v(cK), make_float2(pz0, pz1)), f2mul(im, im));
+                        const float2 t2 = __ffma2_rn(f2mul(f2v(m2s2), im), make_float2(a0.x, a1.x), t1);
+                        g = __ffma2_rn(f2v(s2), make_float2(a0.y, a1.y), t2);
                     }
                     const int pc0 = (ty + 2) * PW + tx + 2;
                     const float *pm = phi_at(2 * kk - 1), *p0 = phi_at(2 * kk), *p1 = phi_at(2 * kk + 1),
@@ -1231,11 +1235,10 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
                               f2sub(make_float2(n1[NZ + nc0], np1[NZ + nc0]), make_float2(nm[NZ + nc0], n0[NZ + nc0]))),
                         f2v(0.5f));
                     const float2 den = __ffma2_rn(ph, ph, f2v(eps2));
-                    const float2 del = f2mul(f2v(eps_pi), make_float2(rcp_approx(den.x), rcp_approx(den.y)));  // Eq. (14)
-                    const float2 pn = __ffma2_rn(
-                        f2v(dt), __ffma2_rn(del, __ffma2_rn(f2v(nu), kap, make_float2(-g.x, -g.y)),
-                                            f2mul(f2v(mu), f2sub(lap, kap))),
-                        ph);
+                    // dt delta (Eq. 14), then phi + dt mu (L - kappa) + dt delta (nu kappa - g) (Eqs. 1, 13)
+                    const float2 dtdel = f2mul(f2v(dt_eps_pi), make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+                    const float2 pn = __ffma2_rn(f2v(dt_mu), f2sub(lap, kap),
+                                                 __ffma2_rn(dtdel, __ffma2_rn(f2v(nu), kap, make_float2(-g.x, -g.y)), ph));
                     const float2 qn = heaviside_q_fast2(pn, eps);
                     phi_out[zoff] = pn.x;
                     q_out[zoff] = qn.x;
@@ -1243,7 +1246,7 @@ __global__ void __launch_bounds__(kZThreads, tbz_deep<R>() ? 2 : 3) k_tb_z(Group
                         phi_out[zoff + plane] = pn.y;
                         q_out[zoff + plane] = qn.y;
                     }
-                    if (dump) {
+                    if constexpr (DUMP) {
                         const long long q0 = colp + (long long)zoff, q1 = q0 + (long long)plane;
                         dump[2 * n + q0] = g.x;
                         dump[3 * n + q0] = kap.x;

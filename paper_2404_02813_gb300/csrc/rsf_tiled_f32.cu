@@ -16,17 +16,25 @@ cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStr
         t.R = 0;
         t.g[0] = 1.f;
     }
-    k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem<R>(), s>>>(G, tap_pairs(t));
+    if (g.dump)
+        k_tb_z<R, ImgT, true><<<g.ncta[3], kZThreads, tbz_smem<R>(), s>>>(G, tap_pairs(t));
+    else
+        k_tb_z<R, ImgT><<<g.ncta[3], kZThreads, tbz_smem<R>(), s>>>(G, tap_pairs(t));
     return cudaGetLastError();
+}
+template <int R, bool DUMP>
+cudaError_t prepare_bz_d() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint8_t, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tbz_smem<R>())) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint16_t, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)tbz_smem<R>())) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tb_z<R, float, DUMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>());
 }
 template <int R>
 cudaError_t prepare_bz_i() {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>())) !=
-        cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_tb_z<R, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>())) !=
-        cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tb_z<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbz_smem<R>());
+    const cudaError_t e = prepare_bz_d<R, false>();
+    return e != cudaSuccess ? e : prepare_bz_d<R, true>();
 }
 template <int R>
 cudaError_t launch_bz_i(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
