@@ -205,8 +205,10 @@ struct ProAB {  // (a, b) as stored by rsf_ta_z (pitched)
     }
 };
 
-// Shared-memory layout of the x/y kernel (float2 units).
-template <int R, int NP>
+// Shared-memory layout of the x/y kernel (float2 units): the input tile of NP
+// pairs and the x-convolved rows of XCP pairs (NP, or 1 when the pairs pass
+// through the x and y convolutions one after the other).
+template <int R, int NP, int XCP = NP>
 struct XYLayout {
     static constexpr int W = kXYT + 2 * R;              // loaded width
     static constexpr int H = kXYT + 2 * R;              // loaded rows
@@ -215,7 +217,7 @@ struct XYLayout {
     // distinct banks
     static constexpr int P = ((W + 15) / 16) * 16 + 2;
     static constexpr int IN = NP * H * P;               // input tile
-    static constexpr int XC = NP * H * kXYT;            // x-convolved rows
+    static constexpr int XC = XCP * H * kXYT;           // x-convolved rows
     static constexpr size_t bytes = sizeof(float2) * (IN + XC);
 };
 
@@ -355,10 +357,20 @@ struct VecLoaderH {  // NP = 1: (H I~, H); NP = 2: also ((1-H) I~, 1-H) (the Eq.
 // tile (x0, y0).  The global loads of plane z+1 are issued right after the
 // first barrier of plane z and land in registers while the convolutions run.
 // `Out` writes the NP pairs (pitch out.px).
+// Two pairs pass through the x and y convolutions one after the other (one
+// pair of x-convolved rows in shared memory) where that lets three CTAs share
+// an SM: radius >= 10.
+template <int R, int NP>
+constexpr bool xy_seq() { return NP == 2 && R >= 10; }
+template <int R, int NP>
+constexpr size_t xy_smem() { return XYLayout<R, NP, xy_seq<R, NP>() ? 1 : NP>::bytes; }
+
 template <int R, int NP, class Loader, class Out>
 __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int ny, int nz, int x0, int y0, int za,
                                         int np, const TapPairs &t, float2 *sm) {
-    using L = XYLayout<R, NP>;
+    constexpr bool SEQ = xy_seq<R, NP>();
+    constexpr int NPX = SEQ ? 1 : NP;        // pairs per x/y round
+    using L = XYLayout<R, NP, NPX>;
     constexpr int T = 2 * R + 1;
     constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
     constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
@@ -372,19 +384,22 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
         ld.store(in);
         __syncthreads();
         if (z + 1 < zb_end) ld.fetch(z + 1);
+#pragma unroll
+        for (int ps = 0; ps < NP / NPX; ++ps) {  // rounds of NPX pairs (one round unless SEQ)
         {
             const int h = lane >> 4, r = (lane >> 2) & 3, g = lane & 3;
             // items (8 rows x 16 columns of one pair) dealt to the warps round-robin; at radius
             // <= 6 and for two pairs a warp's items warp + 8 i run in a compile-time number of
             // rounds (measured faster there; slower at radius 8 with one pair)
-            constexpr int NITEMS = NP * NRB * 2, NW8 = kXYThreads / 32;
+            constexpr int NITEMS = NPX * NRB * 2, NW8 = kXYThreads / 32;
             constexpr bool STATIC = R <= 6 || NP == 2;
             constexpr int NROUNDS = STATIC ? (NITEMS + NW8 - 1) / NW8 : 1;
 #pragma unroll
             for (int i = 0; i < NROUNDS; ++i)
             for (int item = warp + NW8 * i; item < NITEMS; item += STATIC ? NITEMS : NW8) {
-                const int p = item / (NRB * 2);
-                const int rem = item - p * NRB * 2;
+                const int pl = item / (NRB * 2);  // pair within the round
+                const int p = SEQ ? ps : pl;       // pair of the input tile
+                const int rem = item - pl * NRB * 2;
                 const int row = (rem >> 1) * 8 + h * 4 + r;
                 const int xo = (rem & 1) * 16 + g * XT;
                 if (row < L::H) {
@@ -407,16 +422,16 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
                         }
                     }
 #pragma unroll
-                    for (int o = 0; o < XT; ++o) xc[(p * L::H + row) * kXYT + xo + o] = acc[o];
+                    for (int o = 0; o < XT; ++o) xc[(pl * L::H + row) * kXYT + xo + o] = acc[o];
                 }
             }
         }
         __syncthreads();
         {
             const int gx = x0 + lane;
-            float2 res[NP][YT];
+            float2 res[NPX][YT];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) {
+            for (int p = 0; p < NPX; ++p) {
 #pragma unroll
                 for (int o = 0; o < YT; ++o) res[p][o] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -431,11 +446,18 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
                 const int gy0 = y0 + warp * YT;
                 const auto op = out.plane(z);
 #pragma unroll
-                for (int o = 0; o < YT; ++o)
-                    if (gy0 + o < ny) out(op, (gy0 + o) * out.px + gx, res[0][o], res[NP - 1][o]);
+                for (int o = 0; o < YT; ++o) {
+                    if (gy0 + o < ny) {
+                        if constexpr (SEQ)
+                            out.half(op, (gy0 + o) * out.px + gx, ps, res[0][o]);
+                        else
+                            out(op, (gy0 + o) * out.px + gx, res[0][o], res[NPX - 1][o]);
+                    }
+                }
             }
         }
-        __syncthreads();  // the next plane reuses the tiles
+        __syncthreads();  // the next round or plane reuses the tiles
+        }
     }
 }
 
@@ -457,6 +479,10 @@ struct OutF4 {  // two x/y-convolved pairs interleaved per voxel (16 bytes), FP3
     __device__ __forceinline__ void operator()(float4 *pl, int o, float2 a, float2 b) const {
         pl[o] = make_float4(a.x, a.y, b.x, b.y);
     }
+    // pair p alone (the pairs convolved one after the other): its half of the voxel's 16 bytes
+    __device__ __forceinline__ void half(float4 *pl, int o, int p, float2 v) const {
+        reinterpret_cast<float2 *>(pl + o)[p] = v;
+    }
 };
 
 // CTA -> (brick, tile) for the x/y kernels: tiles (tx, ty, tz) of 32 x 32 x xy_planes(B).
@@ -474,7 +500,7 @@ __device__ __forceinline__ XYTile xy_tile_of(const GroupArgs &G, const BrickDev 
 // ((H I~, H), ((1-H) I~, 1-H)) interleaved per voxel into B.u2 read as float4
 // (the Eq. (15) form, which convolves the complement directly).
 template <int R, class ImgT, int NP = 1>
-__global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <= 8 ? 3 : 2))
+__global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <= 8 || xy_seq<R, NP>() ? 3 : 2))
     k_ta_xy(GroupArgs G, TapPairs t) {
     extern __shared__ float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);

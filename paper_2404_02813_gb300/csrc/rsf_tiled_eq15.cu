@@ -21,7 +21,7 @@ int &az4_persist() {
 template <int R>
 cudaError_t prepare_eq15_r() {
     cudaError_t e;
-    constexpr int sm = (int)XYLayout<R, 2>::bytes;
+    constexpr int sm = (int)xy_smem<R, 2>();
     if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint8_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
         cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_ta_xy<R, uint16_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
@@ -46,7 +46,7 @@ cudaError_t launch_eq15_r(const TiledGroup &g, int parity, Profiler *prof, cudaS
     {
         ProfScope ps(prof, KID_TA_XY);
         G.starts = g.starts[0];
-        constexpr size_t sm = XYLayout<R, 2>::bytes;
+        constexpr size_t sm = xy_smem<R, 2>();
         switch (g.imgtype) {
             case 0: k_ta_xy<R, uint8_t, 2><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
             case 1: k_ta_xy<R, uint16_t, 2><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
