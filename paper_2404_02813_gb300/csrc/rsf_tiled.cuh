@@ -213,11 +213,12 @@ struct XYLayout {
     static constexpr int W = kXYT + 2 * R;              // loaded width
     static constexpr int H = kXYT + 2 * R;              // loaded rows
     // row pitch = 2 (mod 16) float2: rows start 16-byte aligned, and the x pass's
-    // 16-byte window reads (lanes: 2 rows x 4 column groups per 8-lane phase) hit
-    // distinct banks
+    // 16-byte window reads (an 8-lane phase covers 2 rows x 4 column groups 8 floats
+    // apart, or 4 rows x 2 groups 16 floats apart) hit distinct banks
     static constexpr int P = ((W + 15) / 16) * 16 + 2;
     static constexpr int IN = NP * H * P;               // input tile
-    static constexpr int XC = XCP * H * kXYT;           // x-convolved rows
+    // x-convolved rows, room for a row pitch of up to 34 (XYCfg)
+    static constexpr int XC = XCP * H * (kXYT + 2);
     static constexpr size_t bytes = sizeof(float2) * (IN + XC);
 };
 
@@ -365,15 +366,34 @@ constexpr bool xy_seq() { return NP == 2 && R >= 10; }
 template <int R, int NP>
 constexpr size_t xy_smem() { return XYLayout<R, NP, xy_seq<R, NP>() ? 1 : NP>::bytes; }
 
-template <int R, int NP, class Loader, class Out>
+// x phase of the x/y kernel: XT outputs per thread and the row pitch XS of the
+// x-convolved rows.  XT = 8: items of 8 rows x 32 columns, each 8-lane phase of
+// a 16-byte window read covering 4 rows x 2 column groups, stores of two outputs
+// (16 bytes) at pitch 34, so that both fall on distinct banks (37 % fewer
+// shared-load wavefronts than XT = 4 at radius 6).  XT = 4 in the single-pair
+// (H I~, H) kernel, whose loader keeps more registers live (XT = 8 measured no
+// faster there): items of 8 rows x 16 columns, 64-bit stores at pitch 33 (rows
+// r..r+3 of a half-warp, four columns apart, on 32 distinct banks; a pitch of 32
+// puts 8 rows on one bank set), pitch 32 at radius >= 10 (measured 8 % faster:
+// its schedule under the 80-register cap differs).
+template <int R, int NP, bool HLOAD>
+struct XYCfg {
+    static constexpr bool H1 = HLOAD && NP == 1;
+    static constexpr int XT = H1 ? 4 : 8;
+    static constexpr int XS = XT == 8 ? kXYT + 2 : (R >= 10 ? kXYT : kXYT + 1);
+};
+
+template <int R, int NP, class Cfg, class Loader, class Out>
 __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int ny, int nz, int x0, int y0, int za,
                                         int np, const TapPairs &t, float2 *sm) {
     constexpr bool SEQ = xy_seq<R, NP>();
     constexpr int NPX = SEQ ? 1 : NP;        // pairs per x/y round
     using L = XYLayout<R, NP, NPX>;
     constexpr int T = 2 * R + 1;
-    constexpr int XT = 4, YT = 4;            // outputs per thread in the x and y phases
+    constexpr int XT = Cfg::XT, XS = Cfg::XS, YT = 4;  // outputs per thread in the x and y phases; pitch
+    static_assert((XT == 4 && XS <= kXYT + 1) || (XT == 8 && XS == kXYT + 2), "x phase layout");
     constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
+    constexpr int NCB = kXYT / (4 * XT);     // column blocks of an item row
     float2 *in = sm;
     float2 *xc = sm + L::IN;
 
@@ -387,21 +407,23 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
 #pragma unroll
         for (int ps = 0; ps < NP / NPX; ++ps) {  // rounds of NPX pairs (one round unless SEQ)
         {
-            const int h = lane >> 4, r = (lane >> 2) & 3, g = lane & 3;
-            // items (8 rows x 16 columns of one pair) dealt to the warps round-robin; at radius
+            const int h = lane >> 4;
+            const int r = XT == 8 ? (lane >> 1) & 3 : (lane >> 2) & 3;
+            const int g = XT == 8 ? (lane & 1) | ((lane >> 2) & 2) : lane & 3;
+            // items (8 rows x 4 XT columns of one pair) dealt to the warps round-robin; at radius
             // <= 6 and for two pairs a warp's items warp + 8 i run in a compile-time number of
             // rounds (measured faster there; slower at radius 8 with one pair)
-            constexpr int NITEMS = NPX * NRB * 2, NW8 = kXYThreads / 32;
+            constexpr int NITEMS = NPX * NRB * NCB, NW8 = kXYThreads / 32;
             constexpr bool STATIC = R <= 6 || NP == 2;
             constexpr int NROUNDS = STATIC ? (NITEMS + NW8 - 1) / NW8 : 1;
 #pragma unroll
             for (int i = 0; i < NROUNDS; ++i)
             for (int item = warp + NW8 * i; item < NITEMS; item += STATIC ? NITEMS : NW8) {
-                const int pl = item / (NRB * 2);  // pair within the round
-                const int p = SEQ ? ps : pl;       // pair of the input tile
-                const int rem = item - pl * NRB * 2;
-                const int row = (rem >> 1) * 8 + h * 4 + r;
-                const int xo = (rem & 1) * 16 + g * XT;
+                const int pl = item / (NRB * NCB);  // pair within the round
+                const int p = SEQ ? ps : pl;         // pair of the input tile
+                const int rem = item - pl * NRB * NCB;
+                const int row = (rem / NCB) * 8 + h * 4 + r;
+                const int xo = (rem % NCB) * 16 + g * XT;
                 if (row < L::H) {
                     const float4 *src = reinterpret_cast<const float4 *>(in + (p * L::H + row) * L::P + xo);
                     // streamed: each loaded pair feeds the outputs it contributes to
@@ -421,8 +443,16 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
                                 if (j - o >= 0 && j - o < T) acc[o] = f2fma(t.g[j - o], v, acc[o]);
                         }
                     }
+                    float2 *dst = xc + (pl * L::H + row) * XS + xo;
+                    if constexpr (XT == 8) {
 #pragma unroll
-                    for (int o = 0; o < XT; ++o) xc[(pl * L::H + row) * kXYT + xo + o] = acc[o];
+                        for (int o = 0; o < XT; o += 2)
+                            *reinterpret_cast<float4 *>(dst + o) =
+                                make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
+                    } else {
+#pragma unroll
+                        for (int o = 0; o < XT; ++o) dst[o] = acc[o];
+                    }
                 }
             }
         }
@@ -436,7 +466,7 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
                 for (int o = 0; o < YT; ++o) res[p][o] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < YT + 2 * R; ++j) {
-                    const float2 v = xc[(p * L::H + warp * YT + j) * kXYT + lane];
+                    const float2 v = xc[(p * L::H + warp * YT + j) * XS + lane];
 #pragma unroll
                     for (int o = 0; o < YT; ++o)
                         if (j - o >= 0 && j - o < T) res[p][o] = f2fma(t.g[j - o], v, res[p][o]);
@@ -518,7 +548,7 @@ __global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <=
         if (B.nx % 4 == 0 && reinterpret_cast<uintptr_t>(q) % 16 == 0 &&
             reinterpret_cast<uintptr_t>(img) % (4 * sizeof(ImgT)) == 0) {
             VecLoaderH<R, ImgT, NP> ld(q, img, inv_s, nms, B.nx, B.ny, tl.x0, tl.y0);
-            xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
+            xy_tile<R, NP, XYCfg<R, NP, true>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
             return;
         }
     }
@@ -529,7 +559,7 @@ __global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <=
     pro.inv_s = inv_s;
     pro.nms = nms;
     ScalarLoader<R, NP, Pro> ld(pro, B.nx, B.ny, B.nx, tl.x0, tl.y0);
-    xy_tile<R, NP>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
+    xy_tile<R, NP, XYCfg<R, NP, true>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
 }
 
 template <int R, class S>
@@ -541,7 +571,7 @@ __global__ void __launch_bounds__(kXYThreads, 3) k_tb_xy(GroupArgs G, TapPairs t
     ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
     ScalarLoader<R, 1, ProAB<S>> ld(pro, B.nx, B.ny, B.px, tl.x0, tl.y0);
-    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
+    xy_tile<R, 1, XYCfg<R, 1, false>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
 }
 
 // ------------------------------------------------------------------ A: z
@@ -825,7 +855,7 @@ __global__ void __launch_bounds__(kXYThreads) k_ki_xy(BrickDev B, TapPairs t) {
     ProI<ImgT> pro{reinterpret_cast<const ImgT *>(B.img), B.cs[1], -B.cs[0] * B.cs[1]};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
     ScalarLoader<R, 1, ProI<ImgT>> ld(pro, B.nx, B.ny, B.nx, tx * kXYT, (r % nty) * kXYT);
-    xy_tile<R, 1>(ld, out, B.nx, B.ny, B.nz, tx * kXYT, (r % nty) * kXYT, (r / nty) * xy_planes(B), xy_planes(B), t, sm);
+    xy_tile<R, 1, XYCfg<R, 1, false>>(ld, out, B.nx, B.ny, B.nz, tx * kXYT, (r % nty) * kXYT, (r / nty) * xy_planes(B), xy_planes(B), t, sm);
 }
 
 template <int R>
