@@ -48,7 +48,9 @@ typedef int32_t rsf_status;
 #define RSF_SUSPENDED 2      /* final status of a suspended serving request (rsf_suspend) */
 #define RSF_E_INVAL (-1)     /* bad argument: null pointer, dim < 4, NaN or non-positive sigma/eps/dt, iters < 0 */
 #define RSF_E_NOMEM (-2)     /* the HBM budget or a device allocation was exceeded */
-#define RSF_E_CUDA (-3)      /* a CUDA runtime call failed; see rsf_last_error() */
+#define RSF_E_CUDA (-3)      /* a CUDA runtime call failed, or a kernel's bounded wait for its
+                                TMA copies expired (the context then stays in error: destroy
+                                it); see rsf_last_error() */
 #define RSF_E_TIMEOUT (-4)   /* rsf_wait: its time limit expired before a final status */
 #define RSF_E_NOTFOUND (-5)  /* unknown ticket */
 #define RSF_E_BUSY (-6)      /* queue full */
@@ -279,6 +281,14 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
  *                   unwritten, queued ones are served afterwards; 0: off.
  *                   (A failed launch of a tick is handled the same way.)  Read
  *                   when the serving loop starts (the first rsf_submit).
+ *   RSF_OPT_FAULT_WAIT  1: the z pass of group A arms each of its copy barriers
+ *                   for 16 bytes more than its TMA copies deliver, so that its
+ *                   bounded waits run out (1 s, then 1 s more for the copies in
+ *                   flight) and the kernel records the expiry in the context's
+ *                   error word: the call returns RSF_E_CUDA, and so does every
+ *                   later call on the context (for testing the device-side
+ *                   failure path; no fault is raised); 0 (default): off.  Read
+ *                   per call (per descriptor upload in the serving loop).
  *   RSF_OPT_FORCE   the data terms e_1, e_2 of the force: RSF_FORCE_LI
  *                   (default), Li et al.'s e_i = (K*1) I^2 - 2 I K*f_i +
  *                   K*(f_i^2), read into Eqs. (11)-(12), which convolve the
@@ -313,6 +323,7 @@ rsf_status rsf_step_stages(rsf_ctx *ctx, const void *volume, rsf_dtype vt, int64
 #define RSF_OPT_FORCE 8
 #define RSF_OPT_POISON 9
 #define RSF_OPT_FAULT_UPLOAD 10
+#define RSF_OPT_FAULT_WAIT 11
 #define RSF_FORCE_LI 0
 #define RSF_FORCE_EQ15 1
 #define RSF_PATH_AUTO 0

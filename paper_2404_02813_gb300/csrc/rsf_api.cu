@@ -35,6 +35,17 @@ rsf_status cuda_fail(cudaError_t e, const char *what) {
     return fail(RSF_E_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
+int device_error_code(const rsf_ctx *c) { return c->h_err ? *(volatile const int *)c->h_err : 0; }
+
+rsf_status device_error(const rsf_ctx *c) {
+    const int code = device_error_code(c);
+    if (code == 0) return RSF_OK;
+    return fail(RSF_E_CUDA, "%s (device error word %d); results since are unreliable: destroy the context",
+                code == rsf::kErrWaitExpired ? "a kernel's bounded wait for its TMA copies expired"
+                                             : "a TMA destination in shared memory was misaligned",
+                code);
+}
+
 
 
 extern "C" const char *rsf_last_error(void) { return g_last_error.c_str(); }
@@ -159,6 +170,8 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
         g.nb = nb;
         g.dump = 0;
         for (const rsf::BrickDev &b : gs.bricks) g.dump |= b.dump != nullptr;
+        g.err = c->d_err;
+        g.fault_tx = c->opt_fault_wait ? 16u : 0u;
         const size_t s0 = starts.size();
         starts.resize(s0 + 4 * (size_t)(nb + 1));
         unsigned long long tot[4] = {0, 0, 0, 0};
@@ -176,7 +189,12 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
             g.starts[k] = buf.d_starts + s0 + (size_t)k * (nb + 1);
             g.ncta[k] = (unsigned)tot[k];
         }
-        all.insert(all.end(), gs.bricks.begin(), gs.bricks.end());
+        for (rsf::BrickDev b : gs.bricks) {
+            const cudaError_t e = rsf::tiled_encode_maps(b, gs.force, gs.taps.R);
+            if (e != cudaSuccess) return fail(RSF_E_CUDA, "TMA descriptor of a %dx%dx%d brick: %s", b.nx, b.ny, b.nz,
+                                              cudaGetErrorString(e));
+            all.push_back(b);
+        }
         out->push_back(g);
     }
     RSF_CUDA(cudaMemcpyAsync(buf.d_bricks, all.data(), sizeof(rsf::BrickDev) * all.size(), cudaMemcpyHostToDevice,
@@ -390,6 +408,17 @@ extern "C" rsf_status rsf_create(rsf_ctx **out, int device, uint64_t hbm_budget_
         return cuda_fail(e, "cudaStreamCreate");
     }
     c->prof.stream = c->stream;
+    // the kernels' bounded waits report expiry here: mapped pinned host memory, read by the
+    // host after the synchronisation that ends each call, with no copy
+    e = cudaHostAlloc((void **)&c->h_err, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void **)&c->d_err, c->h_err, 0);
+    if (e != cudaSuccess) {
+        if (c->h_err) cudaFreeHost(c->h_err);
+        cudaStreamDestroy(c->stream);
+        delete c;
+        return cuda_fail(e, "error word");
+    }
+    *c->h_err = 0;
     *out = c;
     return RSF_OK;
 }
@@ -410,6 +439,7 @@ extern "C" void rsf_destroy(rsf_ctx *c) {
         dev_free(c, c->pool, c->pool_cap);
         c->prof.release();
         cudaStreamDestroy(c->stream);
+        cudaFreeHost(c->h_err);
     }
     delete c;
 }
@@ -528,7 +558,7 @@ static rsf_status run(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, 
     if (stages && dump != stages)
         RSF_CUDA(xfer(stages, dump, sizeof(float) * n * RSF_NSTAGES, c->stream));
     RSF_CUDA(cudaStreamSynchronize(c->stream));
-    return RSF_OK;
+    return device_error(c);
 }
 
 extern "C" rsf_status rsf_evolve(rsf_ctx *c, const void *volume, rsf_dtype vt, int64_t nx, int64_t ny, int64_t nz,
@@ -589,6 +619,9 @@ extern "C" rsf_status rsf_set_option(rsf_ctx *c, int32_t key, int64_t value) {
             return RSF_OK;
         case RSF_OPT_POISON:
             c->opt_poison = value != 0;
+            return RSF_OK;
+        case RSF_OPT_FAULT_WAIT:
+            c->opt_fault_wait = value != 0;
             return RSF_OK;
         case RSF_OPT_GRAPH:
             c->opt_graph = value != 0;

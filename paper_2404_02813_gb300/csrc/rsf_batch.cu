@@ -109,7 +109,7 @@ rsf_status time_iteration(rsf_ctx *c, const GroupSpec &g, cudaEvent_t e0, cudaEv
     }
     RSF_CUDA(cudaEventSynchronize(e1));
     RSF_CUDA(cudaEventElapsedTime(ms, e0, e1));
-    return RSF_OK;
+    return device_error(c);
 }
 
 // Pick the group's launch choices by timing iterations, one knob after the other from
@@ -368,7 +368,7 @@ extern "C" rsf_status rsf_evolve_batch(rsf_ctx *c, const rsf_brick *bricks, int3
         if ((st = retire(t))) return st;
     }
     RSF_CUDA(cudaStreamSynchronize(c->stream));
-    return RSF_OK;
+    return device_error(c);
 }
 
 extern "C" rsf_status rsf_autotune_report(rsf_ctx *c, char *buf, int32_t cap) {

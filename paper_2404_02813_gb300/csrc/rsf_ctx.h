@@ -63,6 +63,9 @@ struct rsf_ctx {
     int64_t opt_inject_upload = 0;      // and a descriptor upload of the active set
     int64_t opt_serve_slots = 64;       // bricks the serving loop advances together at most
     int opt_poison = 0;                 // fill working fields with NaN bytes before each solve (tests)
+    int opt_fault_wait = 0;             // z pass of group A expects bytes no copy delivers (tests)
+    int *h_err = nullptr;               // error word of the kernels' bounded waits: mapped pinned host
+    int *d_err = nullptr;               // memory and its device address; nonzero stays (the context is spent)
 };
 
 // One launch group before upload: bricks sharing radius, image type, storage.
@@ -74,6 +77,10 @@ struct GroupSpec {
 
 rsf_status fail(rsf_status st, const char *fmt, ...);
 rsf_status cuda_fail(cudaError_t e, const char *what);
+// The kernels' error word (rsf_ctx::h_err; read after a synchronisation): its
+// value, and RSF_OK or RSF_E_CUDA with a message.
+int device_error_code(const rsf_ctx *c);
+rsf_status device_error(const rsf_ctx *c);
 #define RSF_CUDA(call)                                             \
     do {                                                           \
         cudaError_t e_ = (call);                                   \

@@ -2,6 +2,7 @@
 // kernel translation units of librsf.so.  Not installed; not part of the ABI.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -106,6 +107,10 @@ struct BrickDev {
     int xyp;                // z planes per CTA of the x/y kernels (<= 0: kDefaultXYPlanes)
     int flip;               // this brick's buffer parity is the launch parity xor flip
     float *dump;            // optional 5 * n stage fields (f1, f2, g, kappa, L)
+    // TMA descriptors of group A's z pass (tiled_encode_maps): u2 as FP32 [nz][ny][c nx]
+    // (row pitch c px; c = 2, or 4 in the Eq. (15) form) in boxes of 32 c floats x 1 row x
+    // (64 + 2R) planes, and ki as FP32 [nz][ny][nx] in boxes of 32 x 1 x 64
+    CUtensorMap tm_u, tm_k;
 };
 
 // A set of bricks launched together: same radius, image type and storage.
@@ -119,7 +124,13 @@ struct TiledGroup {
     const int *starts[4];   // device: per kernel, nb + 1 CTA offsets
     unsigned ncta[4];       // CTAs per kernel launch
     int dump;               // 1: some brick has a stage dump (its update kernel writes g, kappa, L)
+    int *err;               // device-visible error word of the kernels' bounded waits (nonzero: expired)
+    unsigned fault_tx;      // bytes the z pass of group A expects beyond its copies (0; > 0 in a fault test)
 };
+
+// Device error word values (TiledGroup::err).
+constexpr int kErrWaitExpired = 1;  // a bounded wait for a TMA copy ran out (1 s)
+constexpr int kErrSmemAlign = 2;    // a TMA destination in shared memory was not 128-byte aligned
 
 constexpr int kDefaultXYPlanes = 16;
 
@@ -129,6 +140,9 @@ bool tiled_supports(int R);
 // bricks of fewer than 2^32 pitched voxels.
 bool tiled_fits(long long nx, long long ny, long long nz);
 int tiled_pitch(int nx);
+// Encodes b.tm_u and b.tm_k (Li's form) or b.tm_u alone (force 1) from b's
+// dimensions, pitch and u2 / ki views, for radius R.
+cudaError_t tiled_encode_maps(BrickDev &b, int force, int R);
 cudaError_t tiled_prepare(int storage, int R, int force);
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
 void tiled_cta_counts(const BrickDev &b, unsigned counts[4]);

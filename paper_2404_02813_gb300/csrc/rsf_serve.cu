@@ -140,6 +140,10 @@ struct Server {
 void CUDART_CB done_cb(void *p) {
     DoneArg *a = static_cast<DoneArg *>(p);
     Server *s = a->srv;
+    // a kernel's bounded wait expired on this context (the error word stays set): the
+    // request's result is unreliable
+    if ((a->status == RSF_OK || a->status == RSF_SUSPENDED) && device_error_code(s->ctx) != 0)
+        a->status = RSF_E_CUDA;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         a->r->t_done = now_s();

@@ -141,6 +141,8 @@ struct GroupArgs {
     const int *starts;  // nb + 1 CTA offsets of this kernel within the launch
     int nb;
     int parity;         // launch parity: a brick reads phi[p], q[p] with p = parity ^ flip, writes the other
+    int *err;           // the group's error word (bounded waits), may be null
+    unsigned fault_tx;  // extra bytes the TMA barriers expect (0; > 0 only in a fault test)
 };
 
 // ---------------------------------------------------------------- x / y
@@ -586,7 +588,7 @@ __global__ void __launch_bounds__(kXYThreads, 3) k_tb_xy(GroupArgs G, TapPairs t
 template <int R>
 constexpr int az_stage() { return (kAZT + 2 * R) * 32 + kAZT * 16; }  // float2 units per stage
 template <int R>
-constexpr size_t az_smem() { return 2 * sizeof(float2) * az_stage<R>(); }
+constexpr size_t az_smem() { return 2 * sizeof(float2) * az_stage<R>() + 2 * sizeof(uint64_t); }  // + barriers
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -602,6 +604,83 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// ---- TMA tile copies completing on shared-memory mbarriers (PTX ISA: mbarrier,
+// cp.async.bulk.tensor).  One thread arms a barrier with the bytes it expects and
+// issues the copies; every thread waits for the phase to complete, for at most
+// kWaitNs (then the kernel reports through the group's error word).
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes initialised barriers visible to the other threads and to the copy unit
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+// one arrival that also raises the phase's expected transaction count by `bytes`
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// waits for the completion of the barrier's phase of the given parity until the
+// global timer passes `deadline`; false if it did not complete by then
+__device__ __forceinline__ bool mbar_wait_until(uint64_t *bar, unsigned parity, unsigned long long deadline) {
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() > deadline) return false;
+    return true;
+}
+// the same for at most kWaitNs from the first failed try (the timer is read only then)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    return mbar_try_wait(bar, parity) || mbar_wait_until(bar, parity, globaltimer_ns() + kWaitNs);
+}
+// orders this thread's earlier generic-proxy accesses to shared memory before
+// later copies of the async proxy (the copy unit) into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// The tensor map at `map` in global memory as it is now (the host rewrites the
+// descriptor array between launches, perhaps over maps the copy unit has seen).
+__device__ __forceinline__ void fence_tensormap(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+// 3-D tile load of the box at element coordinates (x, y, z) of `map` into `dst`
+// (128-byte aligned), completing `bytes of the box` on `bar`.  x times the
+// element size must be a multiple of 16 bytes; y and z may lie outside the
+// tensor (those elements arrive as zeros).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+// records an error in the group's error word (mapped host memory), once per CTA
+__device__ __forceinline__ void report_error(int *err, int code) {
+    if (err && threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(err) = code;
+        __threadfence_system();
+    }
+}
 
 struct AZSlabId {
     int b, x0, y, z0;
@@ -631,29 +710,74 @@ __device__ __forceinline__ AZSlabId az_slab_of(const GroupArgs &G, int slab) {
     return AZSlabId{b, xt * 32, y, zt * kAZT};
 }
 
-// Issues the copies of one slab into `buf`: ROWS x 32 pairs, then kAZT x 32
-// values of K*I~.  Columns past nx lie in the pitch padding (allocated).
-template <int R>
-__device__ __forceinline__ void az_issue(const GroupArgs &G, const AZSlabId &id, float2 *buf) {
-    constexpr int ROWS = kAZT + 2 * R;
-    const BrickDev &B = G.bricks[id.b];
-    const int col = threadIdx.x & 31;
-    const long long pplane = (long long)B.px * B.ny;
-    const long long c0 = (long long)id.y * B.px + id.x0 + col;
-    const int nz = B.nz, row0 = threadIdx.x >> 5;
-    constexpr int kStep = kAZThreads / 32;  // rows per pass of the warps
-    // running source offsets, one plane step per row; rows outside the brick copy
-    // nothing (source size 0) from the field's first element
-    long long off_u = c0 + (long long)(id.z0 - R + row0) * pplane;
-    for (int row = row0; row < ROWS; row += kStep, off_u += kStep * pplane) {
-        const bool ok = (unsigned)(id.z0 - R + row) < (unsigned)nz;
-        cp_async8(buf + row * 32 + col, B.u2 + (ok ? off_u : 0), ok);
+// The persistent slab walk of group A's z kernels: each CTA takes the slabs
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the launch through two stage
+// buffers of STAGE_BYTES in dynamic shared memory, followed by one mbarrier per
+// stage.  Thread 0 issues a slab's TMA copies (issue(id, buf, bar)) one slab
+// ahead, into the stage the previous slab left; every thread waits for its
+// stage's barrier, then body(id, buf) convolves the slab.  The last argument of
+// issue asks it to fence the brick's tensor maps (first slab of each brick).  A wait that runs out
+// (kWaitNs) is reported in the group's error word; the CTA then gives the copies
+// still in flight the same time to land and returns.
+template <int STAGE_BYTES, class Issue, class Body>
+__device__ __forceinline__ void az_walk(const GroupArgs &G, unsigned char *smem, const Issue &issue,
+                                        const Body &body) {
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * STAGE_BYTES);
+    if (smem_addr(smem) % 128u != 0u) {  // the copies' destinations must be 128-byte aligned
+        report_error(G.err, kErrSmemAlign);
+        return;
     }
-    float *kb = reinterpret_cast<float *>(buf + ROWS * 32);
-    long long off_k = c0 + (long long)(id.z0 + row0) * pplane;
-    for (int row = row0; row < kAZT; row += kStep, off_k += kStep * pplane) {
-        const bool ok = id.z0 + row < nz;
-        cp_async4(kb + row * 32 + col, B.ki + (ok ? off_k : 0), ok);
+    const int total = __ldg(G.starts + G.nb);
+    if (threadIdx.x == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned phase = 0u, pending = 0u;  // bit s: parity of stage s's next phase; stage s awaits copies
+    AZSlabId next{};
+    int last_b = -1;  // thread 0: the brick whose maps it fenced last
+    if ((int)blockIdx.x < total) {
+        next = az_slab_of(G, blockIdx.x);
+        if (threadIdx.x == 0) {
+            issue(next, smem, bars, true);
+            last_b = next.b;
+        }
+        pending = 1u;
+    }
+    int stage = 0;
+    bool ok = true;
+    for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
+        const AZSlabId id = next;
+        if (sl + (int)gridDim.x < total) {
+            next = az_slab_of(G, sl + gridDim.x);
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();  // the reads of that stage (before the last barrier) come first
+                issue(next, smem + (stage ^ 1) * STAGE_BYTES, bars + (stage ^ 1), next.b != last_b);
+                last_b = next.b;
+            }
+            pending |= 1u << (stage ^ 1);
+        }
+        if (!mbar_wait(bars + stage, (phase >> stage) & 1u)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u << stage;
+        pending &= ~(1u << stage);
+        body(id, smem + stage * STAGE_BYTES);
+        __syncthreads();  // this stage is refilled by the next iteration's copies
+        stage ^= 1;
+    }
+    if (!ok) {
+        report_error(G.err, kErrWaitExpired);
+        const unsigned long long deadline = globaltimer_ns() + kWaitNs;
+        for (int s = 0; s < 2; ++s)
+            if ((pending >> s) & 1u) mbar_wait_until(bars + s, (phase >> s) & 1u, deadline);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_inval(bars);
+        mbar_inval(bars + 1);
     }
 }
 
@@ -662,85 +786,80 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
     constexpr int T = 2 * R + 1;
     constexpr int ROWS = kAZT + 2 * R;
     constexpr int WIN = kAZO + 2 * R;
-    constexpr int STAGE = az_stage<R>();
+    constexpr int STAGE_BYTES = (int)sizeof(float2) * az_stage<R>();
     using V2 = typename Store<S>::V2;
-    extern __shared__ float2 slab[];  // [2 stages]{[ROWS][32] pairs, [kAZT][32] K*I~}
-    const int total = __ldg(G.starts + G.nb);
+    // [2 stages]{[ROWS][32] pairs, [kAZT][32] K*I~}, then the two barriers
+    extern __shared__ __align__(128) unsigned char az_sm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int stage = 0;
-    AZSlabId next{};
-    if ((int)blockIdx.x < total) {
-        next = az_slab_of(G, blockIdx.x);
-        az_issue<R>(G, next, slab);
-    }
-    cp_async_commit();
-    for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
-        const AZSlabId id = next;
-        if (sl + (int)gridDim.x < total) {
-            next = az_slab_of(G, sl + gridDim.x);
-            az_issue<R>(G, next, slab + (stage ^ 1) * STAGE);
+    // the slab's boxes: ROWS planes of the pair field from plane z0 - R, kAZT planes of K*I~
+    // from z0 (planes outside the brick and columns past nx arrive as zeros)
+    const auto issue = [&](const AZSlabId &id, unsigned char *buf, uint64_t *bar, bool fence) {
+        const BrickDev &B = G.bricks[id.b];
+        if (fence) {
+            fence_tensormap(&B.tm_u);
+            fence_tensormap(&B.tm_k);
         }
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const float2 *buf = slab + stage * STAGE;
+        mbar_arrive_expect_tx(bar, (unsigned)STAGE_BYTES + G.fault_tx);
+        tma_load_3d(buf, &B.tm_u, 2 * id.x0, id.y, id.z0 - R, bar);
+        tma_load_3d(buf + ROWS * 32 * sizeof(float2), &B.tm_k, id.x0, id.y, id.z0, bar);
+    };
+    const auto body = [&](const AZSlabId &id, const unsigned char *sbuf) {
+        const float2 *buf = reinterpret_cast<const float2 *>(sbuf);
         const BrickDev &B = G.bricks[id.b];
         const int x = id.x0 + lane;
         const int zb = warp * kAZO;
         const int bnx = B.nx, bny = B.ny, bnz = B.nz;  // read once: the stores below might alias B
-        if (x < bnx) {
-            const float l1 = B.lambda1, l2 = B.lambda2;
-            float2 w[WIN];
+        if (x >= bnx) return;
+        const float l1 = B.lambda1, l2 = B.lambda2;
+        float2 w[WIN];
 #pragma unroll
-            for (int j = 0; j < WIN; ++j) w[j] = buf[(zb + j) * 32 + lane];
-            const long long pplane = (long long)B.px * bny;
-            const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
-            V2 *ab = reinterpret_cast<V2 *>(B.ab) + off;
-            const float *ki = reinterpret_cast<const float *>(buf + ROWS * 32) + zb * 32 + lane;
-            const float kxy = __ldg(B.prof + x) * __ldg(B.prof + bnx + id.y);
-            float2 res = make_float2(0.f, 0.f);  // rounding residual carried along z (16-bit storage)
-            const float *pz = B.prof + bnx + bny + id.z0 + zb;
-            float *const dump = B.dump;
+        for (int j = 0; j < WIN; ++j) w[j] = buf[(zb + j) * 32 + lane];
+        const long long pplane = (long long)B.px * bny;
+        const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
+        V2 *ab = reinterpret_cast<V2 *>(B.ab) + off;
+        const float *ki = reinterpret_cast<const float *>(buf + ROWS * 32) + zb * 32 + lane;
+        const float kxy = __ldg(B.prof + x) * __ldg(B.prof + bnx + id.y);
+        float2 res = make_float2(0.f, 0.f);  // rounding residual carried along z (16-bit storage)
+        const float *pz = B.prof + bnx + bny + id.z0 + zb;
+        float *const dump = B.dump;
 #pragma unroll
-            for (int o = 0; o < kAZO; ++o) {
-                const int zo = id.z0 + zb + o;
-                if (zo < bnz) {
-                    float2 acc = make_float2(0.f, 0.f);  // (K*(H I~), K*H)
+        for (int o = 0; o < kAZO; ++o) {
+            const int zo = id.z0 + zb + o;
+            if (zo < bnz) {
+                float2 acc = make_float2(0.f, 0.f);  // (K*(H I~), K*H)
 #pragma unroll
-                    for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
-                    const float f1 = __fdividef(acc.x, acc.y);
-                    // K*(1-H) = K*1 - K*H keeps few significant bits once 1-H < ~1e-6 over the
-                    // whole window (phi > ~3e5 there, delta < 4e-12); the fit is then taken as
-                    // f1, the window mean in that limit, so that it stays finite
-                    const float k1 = kxy * __ldg(pz + o), den = k1 - acc.y;
-                    const float f2 = den > 0x1p-20f * k1 ? __fdividef(ki[o * 32] - acc.x, den) : f1;
-                    const float2 v = make_float2(l1 * f1 - l2 * f2, l1 * (f1 * f1) - l2 * (f2 * f2));
-                    if constexpr (std::is_same<S, float>::value) {
-                        *ab = v;
-                    } else {
-                        // 16-bit storage: the rounding residual of each plane is carried into the
-                        // next plane of the column before it is rounded (first-order noise
-                        // shaping along z), so that the stored field's rounding error is a
-                        // difference of neighbours, which the Gaussian of group B averages out
-                        const float2 want = make_float2(v.x + res.x, v.y + res.y);
-                        const V2 st = Store<S>::pack2(want);
-                        const float2 got = Store<S>::unpack2(st);
-                        res = make_float2(want.x - got.x, want.y - got.y);
-                        *ab = st;
-                    }
-                    ab += pplane;
-                    if (dump) {
-                        const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
-                        const long long n = (long long)B.nx * B.ny * B.nz;
-                        dump[q] = f1 * B.cs[3] + B.cs[0];
-                        dump[n + q] = f2 * B.cs[3] + B.cs[0];
-                    }
+                for (int k = 0; k < T; ++k) acc = f2fma(t.g[k], w[o + k], acc);
+                const float f1 = __fdividef(acc.x, acc.y);
+                // K*(1-H) = K*1 - K*H keeps few significant bits once 1-H < ~1e-6 over the
+                // whole window (phi > ~3e5 there, delta < 4e-12); the fit is then taken as
+                // f1, the window mean in that limit, so that it stays finite
+                const float k1 = kxy * __ldg(pz + o), den = k1 - acc.y;
+                const float f2 = den > 0x1p-20f * k1 ? __fdividef(ki[o * 32] - acc.x, den) : f1;
+                const float2 v = make_float2(l1 * f1 - l2 * f2, l1 * (f1 * f1) - l2 * (f2 * f2));
+                if constexpr (std::is_same<S, float>::value) {
+                    *ab = v;
+                } else {
+                    // 16-bit storage: the rounding residual of each plane is carried into the
+                    // next plane of the column before it is rounded (first-order noise
+                    // shaping along z), so that the stored field's rounding error is a
+                    // difference of neighbours, which the Gaussian of group B averages out
+                    const float2 want = make_float2(v.x + res.x, v.y + res.y);
+                    const V2 st = Store<S>::pack2(want);
+                    const float2 got = Store<S>::unpack2(st);
+                    res = make_float2(want.x - got.x, want.y - got.y);
+                    *ab = st;
+                }
+                ab += pplane;
+                if (dump) {
+                    const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
+                    const long long n = (long long)B.nx * B.ny * B.nz;
+                    dump[q] = f1 * B.cs[3] + B.cs[0];
+                    dump[n + q] = f2 * B.cs[3] + B.cs[0];
                 }
             }
         }
-        __syncthreads();  // this stage is refilled by the next iteration's copies
-        stage ^= 1;
-    }
+    };
+    az_walk<STAGE_BYTES>(G, az_sm, issue, body);
 }
 
 // The z pass of the Eq. (15) form: the same x-z slabs and persistent walk,
@@ -751,95 +870,68 @@ __global__ void __launch_bounds__(kAZThreads, R <= 6 ? 3 : 2) k_ta_z(GroupArgs G
 template <int R>
 constexpr int az4_stage() { return (kAZT + 2 * R) * 32; }  // float4 units per stage
 template <int R>
-constexpr size_t az4_smem() { return 2 * sizeof(float4) * az4_stage<R>(); }
-
-template <int R>
-__device__ __forceinline__ void az4_issue(const GroupArgs &G, const AZSlabId &id, float4 *buf) {
-    constexpr int ROWS = kAZT + 2 * R;
-    constexpr int kStep = kAZThreads / 32;  // rows per pass of the warps
-    const BrickDev &B = G.bricks[id.b];
-    const int col = threadIdx.x & 31;
-    const long long pplane = (long long)B.px * B.ny;
-    const long long c0 = (long long)id.y * B.px + id.x0 + col;
-    const int nz = B.nz, row0 = threadIdx.x >> 5;
-    const float4 *u4 = reinterpret_cast<const float4 *>(B.u2);
-    long long off = c0 + (long long)(id.z0 - R + row0) * pplane;
-    for (int row = row0; row < ROWS; row += kStep, off += kStep * pplane) {
-        const bool ok = (unsigned)(id.z0 - R + row) < (unsigned)nz;
-        cp_async16(buf + row * 32 + col, u4 + (ok ? off : 0), ok);
-    }
-}
+constexpr size_t az4_smem() { return 2 * sizeof(float4) * az4_stage<R>() + 2 * sizeof(uint64_t); }  // + barriers
 
 template <int R>
 __global__ void __launch_bounds__(kAZThreads, 2) k_ta_z4(GroupArgs G, TapPairs t) {
     constexpr int T = 2 * R + 1;
     constexpr int WIN = kAZO + 2 * R;
-    constexpr int STAGE = az4_stage<R>();
-    extern __shared__ float4 slab4[];  // [2 stages][ROWS][32]
-    const int total = __ldg(G.starts + G.nb);
+    constexpr int STAGE_BYTES = (int)sizeof(float4) * az4_stage<R>();
+    extern __shared__ __align__(128) unsigned char az_sm[];  // [2 stages][ROWS][32] float4, then the barriers
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int stage = 0;
-    AZSlabId next{};
-    if ((int)blockIdx.x < total) {
-        next = az_slab_of(G, blockIdx.x);
-        az4_issue<R>(G, next, slab4);
-    }
-    cp_async_commit();
-    for (int sl = blockIdx.x; sl < total; sl += gridDim.x) {
-        const AZSlabId id = next;
-        if (sl + (int)gridDim.x < total) {
-            next = az_slab_of(G, sl + gridDim.x);
-            az4_issue<R>(G, next, slab4 + (stage ^ 1) * STAGE);
-        }
-        cp_async_commit();
-        cp_async_wait1();
-        __syncthreads();
-        const float4 *buf = slab4 + stage * STAGE;
+    // the slab's box: ROWS planes of the four fields from plane z0 - R (planes outside the
+    // brick and columns past nx arrive as zeros)
+    const auto issue = [&](const AZSlabId &id, unsigned char *buf, uint64_t *bar, bool fence) {
+        const CUtensorMap *map = &G.bricks[id.b].tm_u;
+        if (fence) fence_tensormap(map);
+        mbar_arrive_expect_tx(bar, (unsigned)STAGE_BYTES + G.fault_tx);
+        tma_load_3d(buf, map, 4 * id.x0, id.y, id.z0 - R, bar);
+    };
+    const auto body = [&](const AZSlabId &id, const unsigned char *sbuf) {
+        const float4 *buf = reinterpret_cast<const float4 *>(sbuf);
         const BrickDev &B = G.bricks[id.b];
         const int x = id.x0 + lane;
         const int zb = warp * kAZO;
-        if (x < B.nx) {
-            // the two pairs one after the other, each over a window of float2 entries
-            // (one float4 window of 8 + 2R entries spills at radius >= 10)
-            float2 acc[2][kAZO];  // (K*(H I~), K*H), (K*((1-H) I~), K*(1-H))
+        if (x >= B.nx) return;
+        // the two pairs one after the other, each over a window of float2 entries
+        // (one float4 window of 8 + 2R entries spills at radius >= 10)
+        float2 acc[2][kAZO];  // (K*(H I~), K*H), (K*((1-H) I~), K*(1-H))
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const float2 *b2 = reinterpret_cast<const float2 *>(buf) + p;
-                float2 w[WIN];
+        for (int p = 0; p < 2; ++p) {
+            const float2 *b2 = reinterpret_cast<const float2 *>(buf) + p;
+            float2 w[WIN];
 #pragma unroll
-                for (int j = 0; j < WIN; ++j) w[j] = b2[2 * ((zb + j) * 32 + lane)];
-#pragma unroll
-                for (int o = 0; o < kAZO; ++o) {
-                    float2 a = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int k = 0; k < T; ++k) a = f2fma(t.g[k], w[o + k], a);
-                    acc[p][o] = a;
-                }
-            }
-            const long long pplane = (long long)B.px * B.ny;
-            const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
-            float2 *fits = B.abxy + off;
-            const int bnz = B.nz;
-            float *const dump = B.dump;
+            for (int j = 0; j < WIN; ++j) w[j] = b2[2 * ((zb + j) * 32 + lane)];
 #pragma unroll
             for (int o = 0; o < kAZO; ++o) {
-                const int zo = id.z0 + zb + o;
-                if (zo < bnz) {
-                    const float f1 = __fdividef(acc[0][o].x, acc[0][o].y), f2 = __fdividef(acc[1][o].x, acc[1][o].y);
-                    *fits = make_float2(f1, f2);
-                    fits += pplane;
-                    if (dump) {
-                        const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
-                        const long long n = (long long)B.nx * B.ny * B.nz;
-                        dump[q] = f1 * B.cs[3] + B.cs[0];
-                        dump[n + q] = f2 * B.cs[3] + B.cs[0];
-                    }
+                float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < T; ++k) a = f2fma(t.g[k], w[o + k], a);
+                acc[p][o] = a;
+            }
+        }
+        const long long pplane = (long long)B.px * B.ny;
+        const long long off = (long long)(id.z0 + zb) * pplane + (long long)id.y * B.px + x;
+        float2 *fits = B.abxy + off;
+        const int bnz = B.nz;
+        float *const dump = B.dump;
+#pragma unroll
+        for (int o = 0; o < kAZO; ++o) {
+            const int zo = id.z0 + zb + o;
+            if (zo < bnz) {
+                const float f1 = __fdividef(acc[0][o].x, acc[0][o].y), f2 = __fdividef(acc[1][o].x, acc[1][o].y);
+                *fits = make_float2(f1, f2);
+                fits += pplane;
+                if (dump) {
+                    const long long q = (long long)zo * B.nx * B.ny + (long long)id.y * B.nx + x;
+                    const long long n = (long long)B.nx * B.ny * B.nz;
+                    dump[q] = f1 * B.cs[3] + B.cs[0];
+                    dump[n + q] = f2 * B.cs[3] + B.cs[0];
                 }
             }
         }
-        __syncthreads();  // this stage is refilled by the next iteration's copies
-        stage ^= 1;
-    }
+    };
+    az_walk<STAGE_BYTES>(G, az_sm, issue, body);
 }
 
 // ------------------------------------------------------- set-up: K*I~
@@ -1360,7 +1452,7 @@ cudaError_t prepare_storage() {
 // One iteration of Li's form (group A, group B, update) for radius R and storage S.
 template <int R, class S>
 cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, nullptr, g.nb, parity};
+    GroupArgs G{g.bricks, nullptr, g.nb, parity, g.err, g.fault_tx};
     const TapPairs tp = tap_pairs(g.taps);
     {
         ProfScope ps(prof, KID_TA_XY);

@@ -41,7 +41,7 @@ cudaError_t prepare_eq15_r() {
 
 template <int R>
 cudaError_t launch_eq15_r(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, nullptr, g.nb, parity};
+    GroupArgs G{g.bricks, nullptr, g.nb, parity, g.err, g.fault_tx};
     const TapPairs tp = tap_pairs(g.taps);
     {
         ProfScope ps(prof, KID_TA_XY);

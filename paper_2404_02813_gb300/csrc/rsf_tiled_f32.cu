@@ -1,6 +1,8 @@
 // rsf_tiled_f32.cu -- instantiates the tiled iteration with FP32 storage (see
 // rsf_tiled.cuh), the storage-independent update kernel, the q set-up kernel
 // and the host-side launch dispatch.
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
+
 #include "rsf_tiled.cuh"
 
 namespace rsf {
@@ -9,7 +11,7 @@ namespace tiled {
 namespace {
 template <int R, class ImgT>
 cudaError_t launch_bz_r(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s) {
-    GroupArgs G{g.bricks, g.starts[3], g.nb, parity};
+    GroupArgs G{g.bricks, g.starts[3], g.nb, parity, g.err, g.fault_tx};
     ProfScope ps(prof, KID_TB_Z);
     Taps t = g.taps;
     if (R == 0) {  // the Eq. (15) form: one unit tap, no convolution of (a, b)
@@ -93,6 +95,55 @@ int tiled_pitch(int nx) { return (nx + tiled::kZX - 1) / tiled::kZX * tiled::kZX
 
 bool tiled_fits(long long nx, long long ny, long long nz) {
     return (long long)tiled_pitch((int)nx) * ny * nz < (1LL << 32);
+}
+
+namespace {
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point (no
+// link against the driver library); null if the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// FP32 view [nz][ny][c nx] of a pitched field with c floats per voxel (row pitch
+// c px floats), read in boxes of 32 c floats x 1 row x `planes` planes.  Elements
+// outside the view (columns >= nx, planes < 0 or >= nz) arrive as zeros.
+cudaError_t encode_slab_map(CUtensorMap *m, const void *base, int c, const BrickDev &b, int planes) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    // the unit's rules: base 16-byte aligned, strides multiples of 16 bytes, boxes of at most
+    // 256 elements per dimension whose rows are a multiple of 16 bytes
+    const unsigned long long row = 4ull * c * b.px;
+    if (!base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || row % 16 != 0 || 32 * c > 256 || planes > 256 ||
+        planes < 1)
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[3] = {(cuuint64_t)c * b.nx, (cuuint64_t)b.ny, (cuuint64_t)b.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)row, (cuuint64_t)row * b.ny};
+    const cuuint32_t box[3] = {(cuuint32_t)(32 * c), 1u, (cuuint32_t)planes};
+    const cuuint32_t elem[3] = {1u, 1u, 1u};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, elem,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace
+
+cudaError_t tiled_encode_maps(BrickDev &b, int force, int R) {
+    const int rows = tiled::kAZT + 2 * R;
+    if (force == 1) {  // the Eq. (15) form: four fields per voxel, no K*I~
+        b.tm_k = CUtensorMap{};
+        return encode_slab_map(&b.tm_u, b.u2, 4, b, rows);
+    }
+    const cudaError_t e = encode_slab_map(&b.tm_u, b.u2, 2, b, rows);
+    return e != cudaSuccess ? e : encode_slab_map(&b.tm_k, b.ki, 1, b, tiled::kAZT);
 }
 
 cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s) {

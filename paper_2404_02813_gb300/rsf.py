@@ -34,6 +34,7 @@ OPT_PATH, OPT_ZCHUNK, OPT_STORAGE, OPT_AUTOTUNE, OPT_GRAPH, OPT_FAULT_ADMISSION,
 OPT_FORCE = 8
 OPT_POISON = 9
 OPT_FAULT_UPLOAD = 10
+OPT_FAULT_WAIT = 11
 PATHS = {"auto": 0, "passes": 1, "tiled": 2}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 # data-term forms: Li et al.'s (default) and the paper's Eq. (15) with sigma_2 = 0
