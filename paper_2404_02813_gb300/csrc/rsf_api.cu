@@ -190,7 +190,7 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
             g.ncta[k] = (unsigned)tot[k];
         }
         for (rsf::BrickDev b : gs.bricks) {
-            const cudaError_t e = rsf::tiled_encode_maps(b, gs.force, gs.taps.R);
+            const cudaError_t e = rsf::tiled_encode_maps(b, gs.force, gs.storage, gs.taps.R);
             if (e != cudaSuccess) return fail(RSF_E_CUDA, "TMA descriptor of a %dx%dx%d brick: %s", b.nx, b.ny, b.nz,
                                               cudaGetErrorString(e));
             all.push_back(b);

@@ -107,10 +107,12 @@ struct BrickDev {
     int xyp;                // z planes per CTA of the x/y kernels (<= 0: kDefaultXYPlanes)
     int flip;               // this brick's buffer parity is the launch parity xor flip
     float *dump;            // optional 5 * n stage fields (f1, f2, g, kappa, L)
-    // TMA descriptors of group A's z pass (tiled_encode_maps): u2 as FP32 [nz][ny][c nx]
+    // TMA descriptors (tiled_encode_maps).  Group A's z pass: u2 as FP32 [nz][ny][c nx]
     // (row pitch c px; c = 2, or 4 in the Eq. (15) form) in boxes of 32 c floats x 1 row x
-    // (64 + 2R) planes, and ki as FP32 [nz][ny][nx] in boxes of 32 x 1 x 64
-    CUtensorMap tm_u, tm_k;
+    // (64 + 2R) planes, and ki as FP32 [nz][ny][nx] in boxes of 32 x 1 x 64.  Group B's x/y
+    // kernel (Li's form, FP32 storage, even R): ab as FP32 [nz][ny][2 nx] in boxes of one
+    // input tile, 2 tiled_xy_in_pitch(R) floats x (32 + 2R) rows x 1 plane
+    CUtensorMap tm_u, tm_k, tm_ab;
 };
 
 // A set of bricks launched together: same radius, image type and storage.
@@ -140,9 +142,13 @@ bool tiled_supports(int R);
 // bricks of fewer than 2^32 pitched voxels.
 bool tiled_fits(long long nx, long long ny, long long nz);
 int tiled_pitch(int nx);
-// Encodes b.tm_u and b.tm_k (Li's form) or b.tm_u alone (force 1) from b's
-// dimensions, pitch and u2 / ki views, for radius R.
-cudaError_t tiled_encode_maps(BrickDev &b, int force, int R);
+// Encodes b's tensor maps from its dimensions, pitch and field views for its
+// group's form (force), storage and radius R: b.tm_u, b.tm_k (Li's form) and
+// b.tm_ab (Li's form, FP32 storage, even R); the others zeroed.
+cudaError_t tiled_encode_maps(BrickDev &b, int force, int storage, int R);
+// Row pitch (float2) of the x/y kernels' input tile for radius R: 32 + 2R
+// rounded up to a multiple of 16, plus 2.
+constexpr int tiled_xy_in_pitch(int R) { return ((32 + 2 * R + 15) / 16) * 16 + 2; }
 cudaError_t tiled_prepare(int storage, int R, int force);
 cudaError_t tiled_iterate(const TiledGroup &g, int parity, Profiler *prof, cudaStream_t s);
 void tiled_cta_counts(const BrickDev &b, unsigned counts[4]);

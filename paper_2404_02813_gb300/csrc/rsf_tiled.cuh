@@ -145,6 +145,83 @@ struct GroupArgs {
     unsigned fault_tx;  // extra bytes the TMA barriers expect (0; > 0 only in a fault test)
 };
 
+// ---- TMA tile copies completing on shared-memory mbarriers (PTX ISA: mbarrier,
+// cp.async.bulk.tensor).  One thread arms a barrier with the bytes it expects and
+// issues the copies; every thread waits for the phase to complete, for at most
+// kWaitNs (then the kernel reports through the group's error word).
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// makes initialised barriers visible to the other threads and to the copy unit
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+// one arrival that also raises the phase's expected transaction count by `bytes`
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// waits for the completion of the barrier's phase of the given parity until the
+// global timer passes `deadline`; false if it did not complete by then
+__device__ __forceinline__ bool mbar_wait_until(uint64_t *bar, unsigned parity, unsigned long long deadline) {
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() > deadline) return false;
+    return true;
+}
+// the same for at most kWaitNs from the first failed try (the timer is read only then)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    return mbar_try_wait(bar, parity) || mbar_wait_until(bar, parity, globaltimer_ns() + kWaitNs);
+}
+// orders this thread's earlier generic-proxy accesses to shared memory before
+// later copies of the async proxy (the copy unit) into it
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// The tensor map at `map` in global memory as it is now (the host rewrites the
+// descriptor array between launches, perhaps over maps the copy unit has seen).
+__device__ __forceinline__ void fence_tensormap(const CUtensorMap *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+// 3-D tile load of the box at element coordinates (x, y, z) of `map` into `dst`
+// (128-byte aligned), completing `bytes of the box` on `bar`.  x times the
+// element size must be a multiple of 16 bytes; y and z may lie outside the
+// tensor (those elements arrive as zeros).
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+// records an error in the group's error word (mapped host memory), once per CTA
+__device__ __forceinline__ void report_error(int *err, int code) {
+    if (err && threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(err) = code;
+        __threadfence_system();
+    }
+}
+
 // ---------------------------------------------------------------- x / y
 
 // A producer of the x/y kernel's input pairs: plane(off) gives the plane at
@@ -217,7 +294,8 @@ struct XYLayout {
     // row pitch = 2 (mod 16) float2: rows start 16-byte aligned, and the x pass's
     // 16-byte window reads (an 8-lane phase covers 2 rows x 4 column groups 8 floats
     // apart, or 4 rows x 2 groups 16 floats apart) hit distinct banks
-    static constexpr int P = ((W + 15) / 16) * 16 + 2;
+    static constexpr int P = tiled_xy_in_pitch(R);
+    static_assert(P == ((W + 15) / 16) * 16 + 2, "input tile pitch");
     static constexpr int IN = NP * H * P;               // input tile
     // x-convolved rows, room for a row pitch of up to 34 (XYCfg)
     static constexpr int XC = XCP * H * (kXYT + 2);
@@ -385,9 +463,12 @@ struct XYCfg {
     static constexpr int XS = XT == 8 ? kXYT + 2 : (R >= 10 ? kXYT : kXYT + 1);
 };
 
-template <int R, int NP, class Cfg, class Loader, class Out>
-__device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int ny, int nz, int x0, int y0, int za,
-                                        int np, const TapPairs &t, float2 *sm) {
+// x then y convolution of plane z of the input tile `in` (NP pairs, row pitch
+// L::P) through the x-convolved rows `xc`, written by `out`; ends with a barrier
+// (both tiles are free again).
+template <int R, int NP, class Cfg, class Out>
+__device__ __forceinline__ void xy_plane(const float2 *in, float2 *xc, const Out &out, int z, int nx, int ny,
+                                         int x0, int y0, const TapPairs &t) {
     constexpr bool SEQ = xy_seq<R, NP>();
     constexpr int NPX = SEQ ? 1 : NP;        // pairs per x/y round
     using L = XYLayout<R, NP, NPX>;
@@ -396,100 +477,106 @@ __device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int 
     static_assert((XT == 4 && XS <= kXYT + 1) || (XT == 8 && XS == kXYT + 2), "x phase layout");
     constexpr int NRB = (L::H + 7) / 8;      // 8-row blocks of the x phase
     constexpr int NCB = kXYT / (4 * XT);     // column blocks of an item row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int ps = 0; ps < NP / NPX; ++ps) {  // rounds of NPX pairs (one round unless SEQ)
+    {
+        const int h = lane >> 4;
+        const int r = XT == 8 ? (lane >> 1) & 3 : (lane >> 2) & 3;
+        const int g = XT == 8 ? (lane & 1) | ((lane >> 2) & 2) : lane & 3;
+        // items (8 rows x 4 XT columns of one pair) dealt to the warps round-robin; at radius
+        // <= 6 and for two pairs a warp's items warp + 8 i run in a compile-time number of
+        // rounds (measured faster there; slower at radius 8 with one pair)
+        constexpr int NITEMS = NPX * NRB * NCB, NW8 = kXYThreads / 32;
+        constexpr bool STATIC = R <= 6 || NP == 2;
+        constexpr int NROUNDS = STATIC ? (NITEMS + NW8 - 1) / NW8 : 1;
+#pragma unroll
+        for (int i = 0; i < NROUNDS; ++i)
+        for (int item = warp + NW8 * i; item < NITEMS; item += STATIC ? NITEMS : NW8) {
+            const int pl = item / (NRB * NCB);  // pair within the round
+            const int p = SEQ ? ps : pl;         // pair of the input tile
+            const int rem = item - pl * NRB * NCB;
+            const int row = (rem / NCB) * 8 + h * 4 + r;
+            const int xo = (rem % NCB) * 16 + g * XT;
+            if (row < L::H) {
+                const float4 *src = reinterpret_cast<const float4 *>(in + (p * L::H + row) * L::P + xo);
+                // streamed: each loaded pair feeds the outputs it contributes to
+                // (output o takes taps k = 0..T-1 in order, as a window would)
+                float2 acc[XT];
+#pragma unroll
+                for (int o = 0; o < XT; ++o) acc[o] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j2 = 0; j2 < (XT + 2 * R) / 2; ++j2) {
+                    const float4 q = src[j2];
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int j = 2 * j2 + h2;
+                        const float2 v = h2 ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+#pragma unroll
+                        for (int o = 0; o < XT; ++o)
+                            if (j - o >= 0 && j - o < T) acc[o] = f2fma(t.g[j - o], v, acc[o]);
+                    }
+                }
+                float2 *dst = xc + (pl * L::H + row) * XS + xo;
+                if constexpr (XT == 8) {
+#pragma unroll
+                    for (int o = 0; o < XT; o += 2)
+                        *reinterpret_cast<float4 *>(dst + o) =
+                            make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
+                } else {
+#pragma unroll
+                    for (int o = 0; o < XT; ++o) dst[o] = acc[o];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    {
+        const int gx = x0 + lane;
+        float2 res[NPX][YT];
+#pragma unroll
+        for (int p = 0; p < NPX; ++p) {
+#pragma unroll
+            for (int o = 0; o < YT; ++o) res[p][o] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < YT + 2 * R; ++j) {
+                const float2 v = xc[(p * L::H + warp * YT + j) * XS + lane];
+#pragma unroll
+                for (int o = 0; o < YT; ++o)
+                    if (j - o >= 0 && j - o < T) res[p][o] = f2fma(t.g[j - o], v, res[p][o]);
+            }
+        }
+        if (gx < nx) {
+            const int gy0 = y0 + warp * YT;
+            const auto op = out.plane(z);
+#pragma unroll
+            for (int o = 0; o < YT; ++o) {
+                if (gy0 + o < ny) {
+                    if constexpr (SEQ)
+                        out.half(op, (gy0 + o) * out.px + gx, ps, res[0][o]);
+                    else
+                        out(op, (gy0 + o) * out.px + gx, res[0][o], res[NPX - 1][o]);
+                }
+            }
+        }
+    }
+    __syncthreads();  // the next round or plane reuses the tiles
+    }
+}
+
+template <int R, int NP, class Cfg, class Loader, class Out>
+__device__ __forceinline__ void xy_tile(Loader &ld, const Out &out, int nx, int ny, int nz, int x0, int y0, int za,
+                                        int np, const TapPairs &t, float2 *sm) {
+    using L = XYLayout<R, NP, xy_seq<R, NP>() ? 1 : NP>;
     float2 *in = sm;
     float2 *xc = sm + L::IN;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int zb_end = min(za + np, nz);
     ld.fetch(za);
     for (int z = za; z < zb_end; ++z) {
         ld.store(in);
         __syncthreads();
         if (z + 1 < zb_end) ld.fetch(z + 1);
-#pragma unroll
-        for (int ps = 0; ps < NP / NPX; ++ps) {  // rounds of NPX pairs (one round unless SEQ)
-        {
-            const int h = lane >> 4;
-            const int r = XT == 8 ? (lane >> 1) & 3 : (lane >> 2) & 3;
-            const int g = XT == 8 ? (lane & 1) | ((lane >> 2) & 2) : lane & 3;
-            // items (8 rows x 4 XT columns of one pair) dealt to the warps round-robin; at radius
-            // <= 6 and for two pairs a warp's items warp + 8 i run in a compile-time number of
-            // rounds (measured faster there; slower at radius 8 with one pair)
-            constexpr int NITEMS = NPX * NRB * NCB, NW8 = kXYThreads / 32;
-            constexpr bool STATIC = R <= 6 || NP == 2;
-            constexpr int NROUNDS = STATIC ? (NITEMS + NW8 - 1) / NW8 : 1;
-#pragma unroll
-            for (int i = 0; i < NROUNDS; ++i)
-            for (int item = warp + NW8 * i; item < NITEMS; item += STATIC ? NITEMS : NW8) {
-                const int pl = item / (NRB * NCB);  // pair within the round
-                const int p = SEQ ? ps : pl;         // pair of the input tile
-                const int rem = item - pl * NRB * NCB;
-                const int row = (rem / NCB) * 8 + h * 4 + r;
-                const int xo = (rem % NCB) * 16 + g * XT;
-                if (row < L::H) {
-                    const float4 *src = reinterpret_cast<const float4 *>(in + (p * L::H + row) * L::P + xo);
-                    // streamed: each loaded pair feeds the outputs it contributes to
-                    // (output o takes taps k = 0..T-1 in order, as a window would)
-                    float2 acc[XT];
-#pragma unroll
-                    for (int o = 0; o < XT; ++o) acc[o] = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int j2 = 0; j2 < (XT + 2 * R) / 2; ++j2) {
-                        const float4 q = src[j2];
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            const int j = 2 * j2 + h2;
-                            const float2 v = h2 ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-#pragma unroll
-                            for (int o = 0; o < XT; ++o)
-                                if (j - o >= 0 && j - o < T) acc[o] = f2fma(t.g[j - o], v, acc[o]);
-                        }
-                    }
-                    float2 *dst = xc + (pl * L::H + row) * XS + xo;
-                    if constexpr (XT == 8) {
-#pragma unroll
-                        for (int o = 0; o < XT; o += 2)
-                            *reinterpret_cast<float4 *>(dst + o) =
-                                make_float4(acc[o].x, acc[o].y, acc[o + 1].x, acc[o + 1].y);
-                    } else {
-#pragma unroll
-                        for (int o = 0; o < XT; ++o) dst[o] = acc[o];
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        {
-            const int gx = x0 + lane;
-            float2 res[NPX][YT];
-#pragma unroll
-            for (int p = 0; p < NPX; ++p) {
-#pragma unroll
-                for (int o = 0; o < YT; ++o) res[p][o] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int j = 0; j < YT + 2 * R; ++j) {
-                    const float2 v = xc[(p * L::H + warp * YT + j) * XS + lane];
-#pragma unroll
-                    for (int o = 0; o < YT; ++o)
-                        if (j - o >= 0 && j - o < T) res[p][o] = f2fma(t.g[j - o], v, res[p][o]);
-                }
-            }
-            if (gx < nx) {
-                const int gy0 = y0 + warp * YT;
-                const auto op = out.plane(z);
-#pragma unroll
-                for (int o = 0; o < YT; ++o) {
-                    if (gy0 + o < ny) {
-                        if constexpr (SEQ)
-                            out.half(op, (gy0 + o) * out.px + gx, ps, res[0][o]);
-                        else
-                            out(op, (gy0 + o) * out.px + gx, res[0][o], res[NPX - 1][o]);
-                    }
-                }
-            }
-        }
-        __syncthreads();  // the next round or plane reuses the tiles
-        }
+        xy_plane<R, NP, Cfg>(in, xc, out, z, nx, ny, x0, y0, t);
     }
 }
 
@@ -564,16 +651,107 @@ __global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <=
     xy_tile<R, NP, XYCfg<R, NP, true>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
 }
 
+// Group B's x/y kernel takes its FP32 (a, b) tile from TMA at even radius: the box's
+// x origin, 2 (x0 - R) floats, is then 16-byte aligned.
+constexpr bool tbxy_tma(int R) { return R % 2 == 0; }
+
+// The single-pair x/y kernel body with the input tile copied by TMA: one box per
+// plane, H rows x P pairs of an FP32 pair field from (x0 - R, y0 - R) -- zeros
+// outside the brick, exactly the convolutions' padding, and the tile's own row
+// pitch, so the x phase reads it as it is.  Two tile stages: plane z + 1 is in
+// flight while plane z is convolved.  Shared memory: the stages (each rounded up
+// to 128 bytes), the x-convolved rows, two mbarriers.  Waits are bounded as in
+// the z pass (expiry reported in the group's error word).
+template <int R>
+struct XYTma {
+    using L = XYLayout<R, 1>;
+    static constexpr int STAGE = (L::IN + 15) / 16 * 16;  // float2 units, a multiple of 128 bytes
+    static constexpr size_t bytes = sizeof(float2) * (2 * STAGE + L::XC) + 2 * sizeof(uint64_t);
+};
+
+template <int R, class Cfg, class Out>
+__device__ __forceinline__ void xy_tile_tma(const GroupArgs &G, const CUtensorMap *map, const Out &out, int nx, int ny,
+                                            int nz, int x0, int y0, int za, int np, const TapPairs &t, float2 *sm) {
+    using L = XYLayout<R, 1>;
+    constexpr int STAGE = XYTma<R>::STAGE;
+    constexpr unsigned BOX = sizeof(float2) * L::IN;  // bytes of one plane's box
+    float2 *xc = sm + 2 * STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(xc + L::XC);
+    if (smem_addr(sm) % 128u != 0u) {
+        report_error(G.err, kErrSmemAlign);
+        return;
+    }
+    const int zb_end = min(za + np, nz);
+    if (threadIdx.x == 0) {
+        mbar_init(bars, 1);
+        mbar_init(bars + 1, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const auto issue = [&](int z, int st) {
+        mbar_arrive_expect_tx(bars + st, BOX + G.fault_tx);
+        tma_load_3d(sm + st * STAGE, map, 2 * (x0 - R), y0 - R, z, bars + st);
+    };
+    unsigned phase = 0u, pending = 0u;  // bit s: parity of stage s's next phase; stage s awaits its copy
+    if (za < zb_end) {
+        if (threadIdx.x == 0) {
+            fence_tensormap(map);
+            issue(za, 0);
+        }
+        pending = 1u;
+    }
+    bool ok = true;
+    for (int z = za; z < zb_end; ++z) {
+        const int st = (z - za) & 1;
+        if (z + 1 < zb_end) {  // the other stage was last read by plane z - 1's x phase, before a barrier
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                issue(z + 1, st ^ 1);
+            }
+            pending |= 1u << (st ^ 1);
+        }
+        if (!mbar_wait(bars + st, (phase >> st) & 1u)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u << st;
+        pending &= ~(1u << st);
+        xy_plane<R, 1, Cfg>(sm + st * STAGE, xc, out, z, nx, ny, x0, y0, t);
+    }
+    if (!ok) {
+        report_error(G.err, kErrWaitExpired);
+        const unsigned long long deadline = globaltimer_ns() + kWaitNs;
+        for (int b = 0; b < 2; ++b)
+            if ((pending >> b) & 1u) mbar_wait_until(bars + b, (phase >> b) & 1u, deadline);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_inval(bars);
+        mbar_inval(bars + 1);
+    }
+}
+
+// Dynamic shared memory of group B's x/y kernel for storage S.
+template <int R, class S>
+constexpr size_t tbxy_smem() {
+    return std::is_same<S, float>::value && tbxy_tma(R) ? XYTma<R>::bytes : XYLayout<R, 1>::bytes;
+}
+
 template <int R, class S>
 __global__ void __launch_bounds__(kXYThreads, 3) k_tb_xy(GroupArgs G, TapPairs t) {
-    extern __shared__ float2 sm[];
+    extern __shared__ __align__(128) float2 sm[];
     const int b = find_brick(G.starts, G.nb, blockIdx.x);
     const BrickDev B = G.bricks[b];
     const XYTile tl = xy_tile_of(G, B, b);
-    ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
     OutF2 out{B.abxy, B.px, (long long)B.px * B.ny};
-    ScalarLoader<R, 1, ProAB<S>> ld(pro, B.nx, B.ny, B.px, tl.x0, tl.y0);
-    xy_tile<R, 1, XYCfg<R, 1, false>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
+    if constexpr (std::is_same<S, float>::value && tbxy_tma(R)) {
+        xy_tile_tma<R, XYCfg<R, 1, false>>(G, &G.bricks[b].tm_ab, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za,
+                                           xy_planes(B), t, sm);
+    } else {
+        ProAB<S> pro{reinterpret_cast<const typename Store<S>::V2 *>(B.ab)};
+        ScalarLoader<R, 1, ProAB<S>> ld(pro, B.nx, B.ny, B.px, tl.x0, tl.y0);
+        xy_tile<R, 1, XYCfg<R, 1, false>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
+    }
 }
 
 // ------------------------------------------------------------------ A: z
@@ -605,82 +783,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, bool vali
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// ---- TMA tile copies completing on shared-memory mbarriers (PTX ISA: mbarrier,
-// cp.async.bulk.tensor).  One thread arms a barrier with the bytes it expects and
-// issues the copies; every thread waits for the phase to complete, for at most
-// kWaitNs (then the kernel reports through the group's error word).
-constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-// makes initialised barriers visible to the other threads and to the copy unit
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
-}
-// one arrival that also raises the phase's expected transaction count by `bytes`
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
-    return t;
-}
-// waits for the completion of the barrier's phase of the given parity until the
-// global timer passes `deadline`; false if it did not complete by then
-__device__ __forceinline__ bool mbar_wait_until(uint64_t *bar, unsigned parity, unsigned long long deadline) {
-    while (!mbar_try_wait(bar, parity))
-        if (globaltimer_ns() > deadline) return false;
-    return true;
-}
-// the same for at most kWaitNs from the first failed try (the timer is read only then)
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-    return mbar_try_wait(bar, parity) || mbar_wait_until(bar, parity, globaltimer_ns() + kWaitNs);
-}
-// orders this thread's earlier generic-proxy accesses to shared memory before
-// later copies of the async proxy (the copy unit) into it
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-// The tensor map at `map` in global memory as it is now (the host rewrites the
-// descriptor array between launches, perhaps over maps the copy unit has seen).
-__device__ __forceinline__ void fence_tensormap(const CUtensorMap *map) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;\n" ::"l"(reinterpret_cast<uint64_t>(map))
-                 : "memory");
-}
-// 3-D tile load of the box at element coordinates (x, y, z) of `map` into `dst`
-// (128-byte aligned), completing `bytes of the box` on `bar`.  x times the
-// element size must be a multiple of 16 bytes; y and z may lie outside the
-// tensor (those elements arrive as zeros).
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-        "[%5];\n" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-        : "memory");
-}
-// records an error in the group's error word (mapped host memory), once per CTA
-__device__ __forceinline__ void report_error(int *err, int code) {
-    if (err && threadIdx.x == 0) {
-        *reinterpret_cast<volatile int *>(err) = code;
-        __threadfence_system();
-    }
-}
 
 struct AZSlabId {
     int b, x0, y, z0;
@@ -1445,8 +1547,7 @@ cudaError_t prepare_storage() {
             cudaSuccess) return e;
         az_persist<R, S>() = sms * (occ > 0 ? occ : 1);
     }
-    return cudaFuncSetAttribute(k_tb_xy<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)XYLayout<R, 1>::bytes);
+    return cudaFuncSetAttribute(k_tb_xy<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbxy_smem<R, S>());
 }
 
 // One iteration of Li's form (group A, group B, update) for radius R and storage S.
@@ -1473,8 +1574,7 @@ cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cuda
     {
         ProfScope ps(prof, KID_TB_XY);
         G.starts = g.starts[2];
-        constexpr size_t sm = XYLayout<R, 1>::bytes;
-        k_tb_xy<R, S><<<g.ncta[2], kXYThreads, sm, s>>>(G, tp);
+        k_tb_xy<R, S><<<g.ncta[2], kXYThreads, tbxy_smem<R, S>(), s>>>(G, tp);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

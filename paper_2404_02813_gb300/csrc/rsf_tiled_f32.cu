@@ -114,20 +114,20 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // FP32 view [nz][ny][c nx] of a pitched field with c floats per voxel (row pitch
-// c px floats), read in boxes of 32 c floats x 1 row x `planes` planes.  Elements
-// outside the view (columns >= nx, planes < 0 or >= nz) arrive as zeros.
-cudaError_t encode_slab_map(CUtensorMap *m, const void *base, int c, const BrickDev &b, int planes) {
+// c px floats), read in boxes of bx floats x by rows x bz planes.  Elements
+// outside the view (columns < 0 or >= nx, rows and planes likewise) arrive as zeros.
+cudaError_t encode_map(CUtensorMap *m, const void *base, int c, const BrickDev &b, int bx, int by, int bz) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     // the unit's rules: base 16-byte aligned, strides multiples of 16 bytes, boxes of at most
     // 256 elements per dimension whose rows are a multiple of 16 bytes
     const unsigned long long row = 4ull * c * b.px;
-    if (!base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || row % 16 != 0 || 32 * c > 256 || planes > 256 ||
-        planes < 1)
+    if (!base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || row % 16 != 0 || (4 * bx) % 16 != 0 || bx < 1 ||
+        bx > 256 || by < 1 || by > 256 || bz < 1 || bz > 256)
         return cudaErrorInvalidValue;
     const cuuint64_t dims[3] = {(cuuint64_t)c * b.nx, (cuuint64_t)b.ny, (cuuint64_t)b.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)row, (cuuint64_t)row * b.ny};
-    const cuuint32_t box[3] = {(cuuint32_t)(32 * c), 1u, (cuuint32_t)planes};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     const cuuint32_t elem[3] = {1u, 1u, 1u};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, elem,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -136,14 +136,17 @@ cudaError_t encode_slab_map(CUtensorMap *m, const void *base, int c, const Brick
 }
 }  // namespace
 
-cudaError_t tiled_encode_maps(BrickDev &b, int force, int R) {
+cudaError_t tiled_encode_maps(BrickDev &b, int force, int storage, int R) {
     const int rows = tiled::kAZT + 2 * R;
-    if (force == 1) {  // the Eq. (15) form: four fields per voxel, no K*I~
-        b.tm_k = CUtensorMap{};
-        return encode_slab_map(&b.tm_u, b.u2, 4, b, rows);
-    }
-    const cudaError_t e = encode_slab_map(&b.tm_u, b.u2, 2, b, rows);
-    return e != cudaSuccess ? e : encode_slab_map(&b.tm_k, b.ki, 1, b, tiled::kAZT);
+    b.tm_k = CUtensorMap{};
+    b.tm_ab = CUtensorMap{};
+    if (force == 1)  // the Eq. (15) form: four fields per voxel, no K*I~, no group B
+        return encode_map(&b.tm_u, b.u2, 4, b, 128, 1, rows);
+    cudaError_t e = encode_map(&b.tm_u, b.u2, 2, b, 64, 1, rows);
+    if (e == cudaSuccess) e = encode_map(&b.tm_k, b.ki, 1, b, 32, 1, tiled::kAZT);
+    if (e == cudaSuccess && storage == 0 && tiled::tbxy_tma(R))
+        e = encode_map(&b.tm_ab, b.ab, 2, b, 2 * tiled_xy_in_pitch(R), 32 + 2 * R, 1);
+    return e;
 }
 
 cudaError_t tiled_q_init(const float *phi, float *q, long long n, float eps, cudaStream_t s) {
