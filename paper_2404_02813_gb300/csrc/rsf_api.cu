@@ -172,6 +172,7 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
         for (const rsf::BrickDev &b : gs.bricks) g.dump |= b.dump != nullptr;
         g.err = c->d_err;
         g.fault_tx = c->opt_fault_wait ? 16u : 0u;
+        g.xy_tma = 1;
         const size_t s0 = starts.size();
         starts.resize(s0 + 4 * (size_t)(nb + 1));
         unsigned long long tot[4] = {0, 0, 0, 0};
@@ -190,9 +191,10 @@ rsf_status upload_groups(rsf_ctx *c, DescBuffers &buf, cudaStream_t stream, cons
             g.ncta[k] = (unsigned)tot[k];
         }
         for (rsf::BrickDev b : gs.bricks) {
-            const cudaError_t e = rsf::tiled_encode_maps(b, gs.force, gs.storage, gs.taps.R);
+            const cudaError_t e = rsf::tiled_encode_maps(b, gs.force, gs.storage, gs.imgtype, gs.taps.R);
             if (e != cudaSuccess) return fail(RSF_E_CUDA, "TMA descriptor of a %dx%dx%d brick: %s", b.nx, b.ny, b.nz,
                                               cudaGetErrorString(e));
+            g.xy_tma &= b.xy_tma;
             all.push_back(b);
         }
         out->push_back(g);

@@ -111,8 +111,11 @@ struct BrickDev {
     // (row pitch c px; c = 2, or 4 in the Eq. (15) form) in boxes of 32 c floats x 1 row x
     // (64 + 2R) planes, and ki as FP32 [nz][ny][nx] in boxes of 32 x 1 x 64.  Group B's x/y
     // kernel (Li's form, FP32 storage, even R): ab as FP32 [nz][ny][2 nx] in boxes of one
-    // input tile, 2 tiled_xy_in_pitch(R) floats x (32 + 2R) rows x 1 plane
-    CUtensorMap tm_u, tm_k, tm_ab;
+    // input tile, 2 tiled_xy_in_pitch(R) floats x (32 + 2R) rows x 1 plane.  Group A's x/y
+    // kernel (Li's form, even R, xy_tma): q[0], q[1] as FP32 [nz][ny][nx] and the image in
+    // its type, in boxes of one staged plane (16-byte aligned column origin, 32 + 2R rows)
+    CUtensorMap tm_u, tm_k, tm_ab, tm_q[2], tm_img;
+    int xy_tma;             // 1: tm_q and tm_img are encoded (rows a multiple of 16 bytes, aligned bases)
 };
 
 // A set of bricks launched together: same radius, image type and storage.
@@ -127,7 +130,8 @@ struct TiledGroup {
     unsigned ncta[4];       // CTAs per kernel launch
     int dump;               // 1: some brick has a stage dump (its update kernel writes g, kappa, L)
     int *err;               // device-visible error word of the kernels' bounded waits (nonzero: expired)
-    unsigned fault_tx;      // bytes the z pass of group A expects beyond its copies (0; > 0 in a fault test)
+    unsigned fault_tx;      // bytes the TMA barriers expect beyond their copies (0; > 0 in a fault test)
+    int xy_tma;             // 1: every brick has xy_tma set; group A's x/y kernel takes its inputs by TMA
 };
 
 // Device error word values (TiledGroup::err).
@@ -145,7 +149,7 @@ int tiled_pitch(int nx);
 // Encodes b's tensor maps from its dimensions, pitch and field views for its
 // group's form (force), storage and radius R: b.tm_u, b.tm_k (Li's form) and
 // b.tm_ab (Li's form, FP32 storage, even R); the others zeroed.
-cudaError_t tiled_encode_maps(BrickDev &b, int force, int storage, int R);
+cudaError_t tiled_encode_maps(BrickDev &b, int force, int storage, int imgtype, int R);
 // Row pitch (float2) of the x/y kernels' input tile for radius R: 32 + 2R
 // rounded up to a multiple of 16, plus 2.
 constexpr int tiled_xy_in_pitch(int R) { return ((32 + 2 * R + 15) / 16) * 16 + 2; }

@@ -651,6 +651,120 @@ __global__ void __launch_bounds__(kXYThreads, NP == 1 ? (R <= 6 ? 4 : 3) : (R <=
     xy_tile<R, NP, XYCfg<R, NP, true>>(ld, out, B.nx, B.ny, B.nz, tl.x0, tl.y0, tl.za, xy_planes(B), t, sm);
 }
 
+// Group A's x/y kernel of Li's form with its inputs copied by TMA (even radius;
+// used for a brick group whose bricks all have q and image rows of a multiple of
+// 16 bytes and aligned bases): per plane one box of q and one of the image land
+// in a staging buffer, each starting at the 16-byte aligned column at or left of
+// x0 - R; a transform pass writes (H I~, H) of the tile from it, two columns per
+// step, zero outside the brick (the copies' zero fill would give H = 1 there),
+// with the arithmetic of the register loaders; the next plane's boxes are then in
+// flight while the tile is convolved.
+template <int R, class ImgT>
+struct XYStageH {
+    static_assert(R % 2 == 0, "even radius: the staged columns' offsets are even");
+    static constexpr int H = kXYT + 2 * R, W = kXYT + 2 * R;
+    static constexpr int RQ = (R + 3) / 4 * 4;                              // q: 4 floats per 16 bytes
+    static constexpr int AI = 16 / (int)sizeof(ImgT);                       // image values per 16 bytes
+    static constexpr int RI = (R + AI - 1) / AI * AI;
+    static constexpr int WQ = kXYT + 2 * RQ, WI = kXYT + 2 * RI;            // box widths (elements)
+    static constexpr int QB = WQ * H * 4, IB = WI * H * (int)sizeof(ImgT);  // box bytes
+    static constexpr int IOFF = (QB + 127) / 128 * 128;                     // image box offset (bytes)
+    static constexpr int BYTES = IOFF + (IB + 127) / 128 * 128;             // staging bytes
+    using L = XYLayout<R, 1>;
+    static constexpr size_t smem = BYTES + sizeof(float2) * (L::IN + L::XC) + sizeof(uint64_t);
+};
+template <class T> struct Pair2;
+template <> struct Pair2<uint8_t> { using V = uchar2; };
+template <> struct Pair2<uint16_t> { using V = ushort2; };
+template <> struct Pair2<float> { using V = float2; };
+
+template <int R, class ImgT>
+__global__ void __launch_bounds__(kXYThreads, R <= 6 ? 4 : 3) k_ta_xy_tma(GroupArgs G, TapPairs t) {
+    using S = XYStageH<R, ImgT>;
+    using L = XYLayout<R, 1>;
+    extern __shared__ __align__(128) unsigned char xsm[];
+    const float *sq = reinterpret_cast<const float *>(xsm);
+    const ImgT *simg = reinterpret_cast<const ImgT *>(xsm + S::IOFF);
+    float2 *tile = reinterpret_cast<float2 *>(xsm + S::BYTES);
+    float2 *xc = tile + L::IN;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(xc + L::XC);
+    const int b = find_brick(G.starts, G.nb, blockIdx.x);
+    const BrickDev &B = G.bricks[b];
+    const XYTile tl = xy_tile_of(G, B, b);
+    const int nx = B.nx, ny = B.ny, nz = B.nz, x0 = tl.x0, y0 = tl.y0, za = tl.za;
+    const float inv_s = B.cs[1], nms = -B.cs[0] * B.cs[1];
+    const CUtensorMap *mq = (G.parity ^ B.flip) ? &B.tm_q[1] : &B.tm_q[0];
+    const CUtensorMap *mi = &B.tm_img;
+    const OutF2 out{B.u2, B.px, (long long)B.px * ny};
+    const int zb_end = min(za + xy_planes(B), nz);
+    if (smem_addr(xsm) % 128u != 0u) {
+        report_error(G.err, kErrSmemAlign);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    const auto issue = [&](int z) {
+        mbar_arrive_expect_tx(bar, (unsigned)(S::QB + S::IB) + G.fault_tx);
+        tma_load_3d(xsm, mq, x0 - S::RQ, y0 - R, z, bar);
+        tma_load_3d(xsm + S::IOFF, mi, x0 - S::RI, y0 - R, z, bar);
+    };
+    bool pending = false;
+    if (za < zb_end) {
+        if (threadIdx.x == 0) {
+            fence_tensormap(mq);
+            fence_tensormap(mi);
+            issue(za);
+        }
+        pending = true;
+    }
+    unsigned phase = 0u;
+    bool ok = true;
+    for (int z = za; z < zb_end; ++z) {
+        if (!mbar_wait(bar, phase)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u;
+        pending = false;
+        constexpr int NPAIRS = S::H * S::W / 2, W2 = S::W / 2;
+#pragma unroll
+        for (int k = 0; k < (NPAIRS + kXYThreads - 1) / kXYThreads; ++k) {
+            const int i = threadIdx.x + k * kXYThreads;
+            if (i < NPAIRS) {
+                const int row = i / W2, col = 2 * (i - row * W2);
+                const float2 qv = *reinterpret_cast<const float2 *>(sq + row * S::WQ + col + (S::RQ - R));
+                const typename Pair2<ImgT>::V iv =
+                    *reinterpret_cast<const typename Pair2<ImgT>::V *>(simg + row * S::WI + col + (S::RI - R));
+                const int gx = x0 - R + col, gy = y0 - R + row;
+                const bool iny = (unsigned)gy < (unsigned)ny;
+                const bool in0 = iny && (unsigned)gx < (unsigned)nx, in1 = iny && (unsigned)(gx + 1) < (unsigned)nx;
+                const float h0 = h_of_q(qv.x), h1 = h_of_q(qv.y);
+                const float v0 = fmaf((float)iv.x, inv_s, nms), v1 = fmaf((float)iv.y, inv_s, nms);
+                *reinterpret_cast<float4 *>(tile + row * L::P + col) =
+                    make_float4(in0 ? h0 * v0 : 0.f, in0 ? h0 : 0.f, in1 ? h1 * v1 : 0.f, in1 ? h1 : 0.f);
+            }
+        }
+        __syncthreads();  // the staging buffer is consumed, the tile complete
+        if (z + 1 < zb_end) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async_smem();
+                issue(z + 1);
+            }
+            pending = true;
+        }
+        xy_plane<R, 1, XYCfg<R, 1, true>>(tile, xc, out, z, nx, ny, x0, y0, t);
+    }
+    if (!ok) {
+        report_error(G.err, kErrWaitExpired);
+        if (pending) mbar_wait_until(bar, phase, globaltimer_ns() + kWaitNs);
+        return;
+    }
+    if (threadIdx.x == 0) mbar_inval(bar);
+}
+
 // Group B's x/y kernel takes its FP32 (a, b) tile from TMA at even radius: the box's
 // x origin, 2 (x0 - R) floats, is then 16-byte aligned.
 constexpr bool tbxy_tma(int R) { return R % 2 == 0; }
@@ -1537,6 +1651,14 @@ cudaError_t prepare_storage() {
                                   (int)XYLayout<R, 1>::bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_ta_xy<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)XYLayout<R, 1>::bytes)) != cudaSuccess) return e;
+    if constexpr (R % 2 == 0) {
+        if ((e = cudaFuncSetAttribute(k_ta_xy_tma<R, uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)XYStageH<R, uint8_t>::smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_ta_xy_tma<R, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)XYStageH<R, uint16_t>::smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_ta_xy_tma<R, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)XYStageH<R, float>::smem)) != cudaSuccess) return e;
+    }
     if ((e = cudaFuncSetAttribute(k_ta_z<R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)az_smem<R>())) !=
         cudaSuccess) return e;
     {
@@ -1559,10 +1681,23 @@ cudaError_t launch_storage(const TiledGroup &g, int parity, Profiler *prof, cuda
         ProfScope ps(prof, KID_TA_XY);
         G.starts = g.starts[0];
         constexpr size_t sm = XYLayout<R, 1>::bytes;
-        switch (g.imgtype) {
-            case 0: k_ta_xy<R, uint8_t><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
-            case 1: k_ta_xy<R, uint16_t><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
-            default: k_ta_xy<R, float><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp);
+        bool staged = false;  // inputs by TMA (every brick's rows allow the copies)
+        if constexpr (R % 2 == 0) {
+            if (g.xy_tma) {
+                staged = true;
+                switch (g.imgtype) {
+                    case 0: k_ta_xy_tma<R, uint8_t><<<g.ncta[0], kXYThreads, XYStageH<R, uint8_t>::smem, s>>>(G, tp); break;
+                    case 1: k_ta_xy_tma<R, uint16_t><<<g.ncta[0], kXYThreads, XYStageH<R, uint16_t>::smem, s>>>(G, tp); break;
+                    default: k_ta_xy_tma<R, float><<<g.ncta[0], kXYThreads, XYStageH<R, float>::smem, s>>>(G, tp);
+                }
+            }
+        }
+        if (!staged) {
+            switch (g.imgtype) {
+                case 0: k_ta_xy<R, uint8_t><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
+                case 1: k_ta_xy<R, uint16_t><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp); break;
+                default: k_ta_xy<R, float><<<g.ncta[0], kXYThreads, sm, s>>>(G, tp);
+            }
         }
     }
     {

@@ -113,39 +113,84 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// FP32 view [nz][ny][c nx] of a pitched field with c floats per voxel (row pitch
-// c px floats), read in boxes of bx floats x by rows x bz planes.  Elements
-// outside the view (columns < 0 or >= nx, rows and planes likewise) arrive as zeros.
-cudaError_t encode_map(CUtensorMap *m, const void *base, int c, const BrickDev &b, int bx, int by, int bz) {
+// The unit's rules for a 3-D tiled map: base 16-byte aligned, row and plane
+// strides multiples of 16 bytes, boxes of 1..256 elements per dimension whose
+// rows are a multiple of 16 bytes.
+bool map_ok(const void *base, unsigned long long row_bytes, int bx, int by, int bz, int esize) {
+    return base && reinterpret_cast<uintptr_t>(base) % 16 == 0 && row_bytes % 16 == 0 &&
+           ((unsigned long long)bx * esize) % 16 == 0 && bx >= 1 && bx <= 256 && by >= 1 && by <= 256 && bz >= 1 &&
+           bz <= 256;
+}
+
+// View [nz][ny][c nx] of a field of `type` elements (esize bytes) with c elements per
+// voxel and a row pitch of c rx elements, read in boxes of bx x by x bz elements.
+// Elements outside the view (columns < 0 or >= c nx, rows and planes likewise)
+// arrive as zeros.
+cudaError_t encode_typed(CUtensorMap *m, CUtensorMapDataType type, int esize, const void *base, int c, int rx,
+                         const BrickDev &b, int bx, int by, int bz) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
-    // the unit's rules: base 16-byte aligned, strides multiples of 16 bytes, boxes of at most
-    // 256 elements per dimension whose rows are a multiple of 16 bytes
-    const unsigned long long row = 4ull * c * b.px;
-    if (!base || reinterpret_cast<uintptr_t>(base) % 16 != 0 || row % 16 != 0 || (4 * bx) % 16 != 0 || bx < 1 ||
-        bx > 256 || by < 1 || by > 256 || bz < 1 || bz > 256)
-        return cudaErrorInvalidValue;
+    const unsigned long long row = (unsigned long long)esize * c * rx;
+    if (!map_ok(base, row, bx, by, bz, esize)) return cudaErrorInvalidValue;
     const cuuint64_t dims[3] = {(cuuint64_t)c * b.nx, (cuuint64_t)b.ny, (cuuint64_t)b.nz};
     const cuuint64_t strides[2] = {(cuuint64_t)row, (cuuint64_t)row * b.ny};
     const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     const cuuint32_t elem[3] = {1u, 1u, 1u};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(base), dims, strides, box, elem,
+    const CUresult r = enc(m, type, 3, const_cast<void *>(base), dims, strides, box, elem,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+// FP32 view [nz][ny][c nx] of a pitched field (row pitch c px floats).
+cudaError_t encode_map(CUtensorMap *m, const void *base, int c, const BrickDev &b, int bx, int by, int bz) {
+    return encode_typed(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, c, b.px, b, bx, by, bz);
+}
+
+// Group A's x/y staging maps (q[0], q[1], the image) of an even-radius brick when
+// its unpitched rows allow them; b.xy_tma says whether they were made.
+template <class ImgT>
+cudaError_t encode_xy_stage(BrickDev &b, CUtensorMapDataType type, int R) {
+    b.xy_tma = 0;
+    switch (R) {
+        case 2: case 4: case 6: case 8: case 10: case 12: break;
+        default: return cudaSuccess;
+    }
+    // the same box geometry as the kernel's staging (XYStageH)
+    const int H = 32 + 2 * R, RQ = (R + 3) / 4 * 4, AI = 16 / (int)sizeof(ImgT), RI = (R + AI - 1) / AI * AI;
+    const int WQ = 32 + 2 * RQ, WI = 32 + 2 * RI;
+    const unsigned long long qrow = 4ull * b.nx, irow = (unsigned long long)sizeof(ImgT) * b.nx;
+    if (!map_ok(b.q[0], qrow, WQ, H, 1, 4) || !map_ok(b.q[1], qrow, WQ, H, 1, 4) ||
+        !map_ok(b.img, irow, WI, H, 1, (int)sizeof(ImgT)))
+        return cudaSuccess;  // not eligible: the register loaders serve this brick's group
+    cudaError_t e = encode_typed(&b.tm_q[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.q[0], 1, b.nx, b, WQ, H, 1);
+    if (e == cudaSuccess) e = encode_typed(&b.tm_q[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, b.q[1], 1, b.nx, b, WQ, H, 1);
+    if (e == cudaSuccess)
+        e = encode_typed(&b.tm_img, type, (int)sizeof(ImgT), b.img, 1, b.nx, b, WI, H, 1);
+    if (e == cudaSuccess) b.xy_tma = 1;
+    return e;
+}
 }  // namespace
 
-cudaError_t tiled_encode_maps(BrickDev &b, int force, int storage, int R) {
+cudaError_t tiled_encode_maps(BrickDev &b, int force, int storage, int imgtype, int R) {
     const int rows = tiled::kAZT + 2 * R;
     b.tm_k = CUtensorMap{};
     b.tm_ab = CUtensorMap{};
+    b.tm_q[0] = b.tm_q[1] = b.tm_img = CUtensorMap{};
+    b.xy_tma = 0;
     if (force == 1)  // the Eq. (15) form: four fields per voxel, no K*I~, no group B
         return encode_map(&b.tm_u, b.u2, 4, b, 128, 1, rows);
     cudaError_t e = encode_map(&b.tm_u, b.u2, 2, b, 64, 1, rows);
     if (e == cudaSuccess) e = encode_map(&b.tm_k, b.ki, 1, b, 32, 1, tiled::kAZT);
     if (e == cudaSuccess && storage == 0 && tiled::tbxy_tma(R))
         e = encode_map(&b.tm_ab, b.ab, 2, b, 2 * tiled_xy_in_pitch(R), 32 + 2 * R, 1);
+    if (e == cudaSuccess) {
+        switch (imgtype) {
+            case 0: e = encode_xy_stage<uint8_t>(b, CU_TENSOR_MAP_DATA_TYPE_UINT8, R); break;
+            case 1: e = encode_xy_stage<uint16_t>(b, CU_TENSOR_MAP_DATA_TYPE_UINT16, R); break;
+            default: e = encode_xy_stage<float>(b, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, R);
+        }
+    }
     return e;
 }
 
