@@ -61,11 +61,11 @@ PAPER_TABLE1_GVOX_IT_S = 1.25e8 / 0.585 / 1e9
 # DRAM traffic per voxel measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum
 # per launch / voxels), keyed by kernel, with the SHA-256 of the kernel source file
 # it was captured from; reported only while that file is unchanged.
-NCU_SHA = "32add19e7993ee93"
+NCU_SHA = "25911c66532ecdf4"
 NCU_TRAFFIC = {
     k: {"bytes_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": NCU_SHA,
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage; scaled by voxels"}
-    for k, v in {"rsf_ta_xy": 13.19, "rsf_ta_z": 19.43, "rsf_tb_xy": 15.28, "rsf_tb_z": 21.95}.items()
+    for k, v in {"rsf_ta_xy": 13.20, "rsf_ta_z": 19.43, "rsf_tb_xy": 15.25, "rsf_tb_z": 21.98}.items()
 }
 
 # Warp instructions issued per voxel measured by ncu (smsp__inst_executed.sum / voxels),
@@ -75,7 +75,7 @@ NCU_TRAFFIC = {
 NCU_INST = {
     k: {"warp_inst_per_voxel": v, "source": "rsf_tiled.cuh", "source_sha": NCU_SHA,
         "capture": "384^3 uint16 light-sheet case, sigma 3, FP32 storage"}
-    for k, v in {"rsf_ta_xy": 3.70, "rsf_ta_z": 2.78, "rsf_tb_xy": 2.89, "rsf_tb_z": 6.39}.items()
+    for k, v in {"rsf_ta_xy": 3.13, "rsf_ta_z": 2.78, "rsf_tb_xy": 2.21, "rsf_tb_z": 6.39}.items()
 }
 SM_SUBPARTITIONS = 4  # warp schedulers per SM, one warp instruction issued per cycle each
 
