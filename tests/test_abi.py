@@ -100,3 +100,23 @@ def test_missing_library_fails_loudly(tmp_path):
             rsf.load_library(str(tmp_path / "librsf.so"))
     finally:
         rsf._lib = saved
+
+
+def test_binding_constants_match_the_header():
+    """Every RSF_OPT_*, RSF_FORCE_*, RSF_PATH_* and status code the header
+    defines has the same value in the binding (the binding passes them through)."""
+    from paper_2404_02813_gb300 import rsf
+    txt = open(os.path.join(ROOT, "include", "rsf.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(RSF_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", txt)}
+    opts = {k[len("RSF_"):]: v for k, v in defs.items() if k.startswith("RSF_OPT_")}
+    assert opts, "no options found in the header"
+    for name, v in opts.items():
+        assert getattr(rsf, name) == v, name
+    for k, v in defs.items():
+        if k.startswith("RSF_FORCE_"):
+            assert rsf.FORCES[k[len("RSF_FORCE_"):].lower()] == v, k
+        elif k.startswith("RSF_PATH_"):
+            assert rsf.PATHS[k[len("RSF_PATH_"):].lower()] == v, k
+    for k in ("RSF_OK", "RSF_E_INVAL", "RSF_E_NOMEM", "RSF_E_CUDA", "RSF_E_TIMEOUT", "RSF_E_CANCELLED"):
+        assert k in defs, k
+    assert defs["RSF_E_CUDA"] == -3 and defs["RSF_OPT_FAULT_WAIT"] == 11
